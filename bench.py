@@ -1,0 +1,358 @@
+#!/usr/bin/env python
+"""Benchmark of the fused two-component Shan-Chen D3Q19 evaporation step.
+
+One benchmark step = one lattice time step (one fused launch) of the workload.
+Default workload: the 128^3 floating droplet (radius 24, centred; sinks at the
+z-boundary planes z = 127 and z = 0; tau = 1, G = 3.6, rho_H = 0.03; FP32
+populations, two-lattice pull layout; seeded +-1e-4 noise). Its populations
+(2 x 319 MB) exceed the 129 MB L2, so no flush is needed between steps.
+
+Metric: MLUPS (million site updates per second, both components per update).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank advances its own copy of the lattice (independent
+problems, no data exchange): weak scaling, value = all ranks' site updates /
+the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES_PER_SITE = {"f32": 304, "f16": 152, "bf16": 152}  # read + write 2 x 19 populations
+PROFILE_FILE = os.path.join(ROOT, "profiles", "k_step_droplet_128.md")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="droplet_128")
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
+    ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--zchunk", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload(name, storage, tile=0, zchunk=0):
+    from paper_1701_03637_gb300.workloads import WORKLOADS
+    params, init = WORKLOADS[name](storage=storage)
+    params.update(tile=tile, zchunk=zchunk)
+    return params, init
+
+
+def describe(name, params, storage):
+    n = params["nx"]
+    geom = {0: "periodic", 1: f"planar sink z={params.get('sink_z0')} x{params.get('sink_layers')} layers",
+            2: f"spherical sink R_H={params.get('R_H')}"}[params.get("geometry", 0)]
+    return (f"{name}: {params['nx']}x{params['ny']}x{params['nz']} two-component D3Q19 Shan-Chen droplet, "
+            f"{geom}, tau=1, G=3.6, rho_H={params['rho_H']}, {storage} populations, two-lattice pull")
+
+
+def source_digest():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1701_03637_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode() + b"\0" + fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload_name, storage):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the
+    current kernel source and this workload; None otherwise."""
+    try:
+        lines = open(PROFILE_FILE).read().splitlines()
+    except OSError:
+        return None
+    kv = {}
+    for ln in lines:
+        if ln.startswith("- ") and ":" in ln:
+            k, v = ln[2:].split(":", 1)
+            kv[k.strip()] = v.strip().strip("`")
+    if kv.get("source_digest") != source_digest() or kv.get("workload") != workload_name or kv.get("storage") != storage:
+        return None
+    try:
+        return float(kv["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def measured_peak_hbm():
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms; keeps the rows taken inside [t0, t1]."""
+
+    FIELDS = ("timestamp,index,pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.path = tempfile.mktemp(prefix="clocks_", suffix=".csv")
+        self.proc = None
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self, t0, t1, bus_id=None):
+        rows = []
+        try:
+            for ln in open(self.path):
+                parts = [p.strip() for p in ln.split(",")]
+                if len(parts) < 11:
+                    continue
+                try:
+                    ts = time.mktime(time.strptime(parts[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                    ts += float("0." + parts[0].split(".")[1]) if "." in parts[0] else 0.0
+                except Exception:
+                    continue
+                if bus_id and bus_id.lower() not in parts[2].lower():
+                    continue
+                if t0 - 0.25 <= ts <= t1 + 0.25:
+                    rows.append(parts)
+        except OSError:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        mx = [float(r[4]) for r in rows if r[4].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[7 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(float(r[5]) for r in rows if r[5].replace(".", "").isdigit()) if rows else None}
+
+
+def oracle_rate(params, init, budget_s, threads):
+    """Time the FP64 oracle as it stands on the host cores: MLUPS over whole-lattice steps."""
+    import oracle
+    oracle.set_threads(threads)
+    o = oracle.Lattice(params)
+    o.init_shape(init)
+    t = time.perf_counter()
+    o.step(1)
+    one = time.perf_counter() - t
+    steps = max(1, int(budget_s / max(one, 1e-6)))
+    t = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t
+    n = params["nx"] * params["ny"] * params["nz"]
+    return n * steps / dt / 1e6, steps
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_reference(args):
+    """The oracle arm: FP64 plain-C oracle on the host cores, one oracle time step of a
+    bounded crop of the workload per benchmark step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_1701_03637_gb300.workloads import droplet
+    params, init = workload(args.workload, args.storage)
+    n_full = params["nx"]
+    cores = host_cores()
+    # calibrate on a small crop, then size the crop so W + K steps take about 90 s
+    probe_edge = 24
+    p_probe, i_probe = droplet(probe_edge, 24.0 * probe_edge / n_full, 1)
+    rate, _ = oracle_rate(p_probe, i_probe, 0.5, cores)
+    sites = rate * 1e6 * 90.0 / max(1, args.steps + args.warmup)
+    edge = int(max(8, min(n_full, round(sites ** (1.0 / 3.0)))))
+    p, i = droplet(edge, 24.0 * edge / n_full, 1)
+    import oracle
+    oracle.set_threads(cores)
+    o = oracle.Lattice(p)
+    o.init_shape(i)
+    o.step(args.warmup)
+    t = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t
+    n = edge ** 3
+    value = n * args.steps / dt / 1e6
+    sample = (f"FP64 oracle (plain C, OpenMP) on a {edge}^3 crop of the {args.workload} workload "
+              f"(same geometry and parameters, radius scaled), one oracle step per benchmark step")
+    out = {"metric": "MLUPS", "value": value, "unit": "MLUPS", "impl": "reference", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": describe(args.workload, params, args.storage), "sample_lattice": f"{edge}^3"},
+           "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_1701_03637_gb300 as sc
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    sc.build()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    params, init = workload(args.workload, args.storage, args.tile, args.zchunk)
+    n = params["nx"] * params["ny"] * params["nz"]
+    lat = sc.Lattice(params)
+    lat.init(init)
+    stream = torch.cuda.current_stream()
+    lat.step(args.warmup)
+    torch.cuda.synchronize()
+    try:
+        bus = torch.cuda.get_device_properties(local).pci_bus_id
+    except Exception:
+        bus = None
+    sampler = ClockSampler()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.time()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    lat.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    t1 = time.time()
+    sampler.stop()
+    ms = e0.elapsed_time(e1)
+    ms_max = max_over_ranks(ms)
+    d = lat.diagnostics()
+    if d["status"] != 0:
+        raise RuntimeError(f"diagnostics status {d['status']} after the timed run")
+
+    sites_total = n * args.steps * world
+    value = sites_total / (ms_max * 1e-3) / 1e6
+    step_s = ms * 1e-3 / args.steps
+    peak, peak_kind = measured_peak_hbm()
+    achieved = BYTES_PER_SITE[args.storage] * n / step_s / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": profiled_traffic(args.workload, args.storage),
+            "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
+            "algorithmic_bytes_per_site": BYTES_PER_SITE[args.storage]}
+
+    # end to end through the public API: initial densities from pinned host memory,
+    # the steps with FP64 diagnostics read back every 100 steps, final densities to host
+    e2e = None
+    if not args.no_e2e:
+        rr0, rb0 = lat.read_fields()
+        h_rr = torch.from_numpy(rr0.reshape(-1).copy()).pin_memory()
+        h_rb = torch.from_numpy(rb0.reshape(-1).copy()).pin_memory()
+        o_rr = torch.empty(n, dtype=torch.float32).pin_memory()
+        o_rb = torch.empty(n, dtype=torch.float32).pin_memory()
+        diag_every = 100
+        barrier()
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        lat.init_fields_from(h_rr, h_rb)
+        done = 0
+        ndiag = 0
+        while done < args.steps:
+            k = min(diag_every, args.steps - done)
+            lat.step(k)
+            done += k
+            lat.diagnostics()
+            ndiag += 1
+        lat.read_fields_into(o_rr, o_rb)
+        torch.cuda.synchronize()
+        w1 = time.perf_counter()
+        barrier()
+        wall = max_over_ranks(w1 - w0)
+        diag_bytes = ndiag * lat.diag_bytes()
+        e2e = {"value": n * args.steps * world / wall / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": 8 * n / args.steps,
+               "d2h_bytes_per_step": (8 * n + diag_bytes) / args.steps,
+               "includes": "init from pinned host densities, all steps, diagnostics every 100 steps, "
+                           "final densities to pinned host"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = host_cores()
+        rate, steps = oracle_rate(params, init, 12.0, cores)
+        cpu = {"value": rate, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+               "sample": f"FP64 oracle (plain C, OpenMP, {cores} threads) on the full "
+                         f"{params['nx']}x{params['ny']}x{params['nz']} lattice of this workload, "
+                         f"{steps} steps after its initial state"}
+
+    if rank == 0:
+        info = lat.launch_info()
+        clk = sampler.summary(t0, t1, bus)
+        out = {"metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
+               "config": {"workload": describe(args.workload, params, args.storage),
+                          "sites": n, "lattices_per_gpu": 1, "l2": "inputs larger than L2 (no flush)",
+                          "tile": f"{info['tile_x']}x{info['tile_y']}", "zchunk": info["zchunk"],
+                          "ctas": info["ctas"], "parallelism": f"independent replicas x{world}"},
+               "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
+               "clocks": clk, "diag": {k: d[k] for k in ("mass_r", "mass_b", "evaporated_mass", "radius")}}
+        print(json.dumps(out))
+    lat.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

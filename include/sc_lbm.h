@@ -1,0 +1,169 @@
+/*
+ * sc_lbm — GB300 (sm_103a) library for the two-component pseudopotential
+ * (Shan-Chen) lattice Boltzmann time step with the fixed-density evaporation
+ * boundary of Hessling, Xie & Harting, "Diffusion dominated evaporation in
+ * multicomponent lattice Boltzmann simulations" (arXiv:1701.03637).
+ *
+ * The method (Sec. II):
+ *   - D3Q19 BGK evolution per component, Eq. (1), toward the second-order
+ *     equilibrium of Eq. (2) with c_s^2 = 1/3, weights 1/3, 1/18, 1/36;
+ *   - densities rho^c = sum_i f_i^c, pseudopotential Psi = 1 - exp(-rho), Eq. (4);
+ *   - inter-component force F^c = -Psi^c(x) g sum_i w_i Psi^cbar(x + e_i) e_i, Eq. (3),
+ *     applied as the velocity shift tau F^c / rho^c on the common velocity;
+ *   - periodic boundaries, halfway bounce-back at solid sites (Sec. II A);
+ *   - evaporation sink (Sec. II C): at sink sites the evaporating component r is
+ *     reset to f_i = w_i rho_H and the other component b to
+ *     f_i = w_i (rho^r + rho^b - rho_H), from the populations that arrived,
+ *     so the total mass is conserved and the evaporated mass is
+ *     sum (rho^r_arrived - rho_H).
+ *
+ * Component 0 ("r") is the paper's evaporating component c, component 1 ("b")
+ * is c-bar, and G is g^{c cbar} = g^{cbar c}.
+ *
+ * Conventions for every call:
+ *   - Return value 0 (SC_OK) on success, a negative SC_E* code otherwise; the
+ *     message of the last failure on the calling thread is in sc_last_error().
+ *   - Lattice site index s = x + nx*(y + ny*z) (x fastest).
+ *   - Population arrays crossing the boundary are canonical: post-streaming,
+ *     post-sink-reset populations f[c][i][s] (c in {0,1}, i in 0..18 in the
+ *     direction order given by sc_lattice_directions).
+ *   - Pointers named *_host are host memory owned by the caller; pointers
+ *     named *_dev are device memory owned by the caller. Calls that touch host
+ *     memory are synchronous with respect to the handle's stream; all other
+ *     calls are asynchronous on that stream.
+ *   - The library never calls exit() or abort(); invalid arguments return
+ *     SC_EINVAL before any device work is queued.
+ */
+#ifndef SC_LBM_H
+#define SC_LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SC_OK 0
+#define SC_EINVAL (-1)      /* invalid argument or parameter combination */
+#define SC_ENOMEM (-2)      /* device or host allocation failed, or caller buffer too small */
+#define SC_ECUDA (-3)       /* a CUDA runtime call failed (message has the CUDA error string) */
+#define SC_ENONFINITE (-4)  /* diagnostics found a NaN/Inf density */
+#define SC_ETIMEOUT (-5)    /* a bounded device-side wait gave up */
+#define SC_ESINKNEG (-6)    /* a sink site had rho^r + rho^b < rho_H (negative complement) */
+
+#define SC_GEOM_PERIODIC 0      /* no sink */
+#define SC_GEOM_PLANAR_SINK 1   /* sink planes z in [sink_z0, sink_z0 + sink_layers) mod nz */
+#define SC_GEOM_SPHERE_SINK 2   /* sink where |x - centre| >= R_H */
+
+#define SC_STORAGE_F32 0        /* FP32 populations */
+#define SC_STORAGE_F16 1        /* FP16 offsets f_i - w_i*rho0 (rho0 = 1), FP32 arithmetic */
+#define SC_STORAGE_BF16 2       /* BF16 offsets f_i - w_i*rho0, FP32 arithmetic */
+
+/* Physical and geometric parameters of one lattice (Sec. II; geometry of Sec. III). */
+typedef struct sc_params {
+  int32_t nx, ny, nz;             /* lattice extent, each >= 1 */
+  double tau_r, tau_b;            /* BGK relaxation times (> 0.5); the paper uses 1 */
+  double G;                       /* g^{c cbar} of Eq. (3) */
+  double rho_H;                   /* imposed density of component r at sink sites */
+  int32_t geometry;               /* SC_GEOM_* */
+  int32_t sink_z0, sink_layers;   /* planar sink: first plane and number of planes (1 or 2) */
+  double sphere_cx, sphere_cy, sphere_cz, R_H;  /* spherical sink: centre and radius */
+  int32_t wall_z0, wall_thickness;/* solid slab z in [wall_z0, wall_z0 + wall_thickness); 0 = none */
+  int32_t storage;                /* SC_STORAGE_* */
+  int32_t tile;                   /* kernel tile choice: 0 = automatic, k > 0 = entry k-1 of sc_tile_list */
+  int32_t zchunk;                 /* planes per CTA along z: 0 = automatic */
+} sc_params;
+
+/* Seeded initial state: film or droplet with uniform noise. */
+typedef struct sc_init {
+  int32_t shape;                  /* 0 = film (r-rich for z < film_z), 1 = droplet (r-rich inside radius) */
+  int32_t film_z;
+  double cx, cy, cz, radius;      /* droplet centre and radius */
+  double rho_hi, rho_lo;          /* majority / minority densities of the initial phases */
+  double noise_amp;               /* each component's density gets U(-a, a) per site */
+  uint64_t seed;                  /* SplitMix64 seed: the noise of (component c, site s) is
+                                     a*(2u - 1), u = (out >> 11) * 2^-53, out = the
+                                     (1 + c*N + s)-th output of SplitMix64(seed) */
+} sc_init;
+
+/* Diagnostics of the canonical state (Sec. III B/C observables). */
+typedef struct sc_diag {
+  int64_t step;                   /* completed time steps */
+  double mass_r, mass_b;          /* FP64 sums of rho over non-solid sites */
+  double evaporated_mass;         /* cumulative sum over steps and sink sites of (rho^r_arrived - rho_H) */
+  double flux_last;               /* the same sum for the last step only */
+  double interface_z;             /* first downward zero of phi(z) = <rho^r - rho^b>_xy above the
+                                     liquid base, linearly interpolated; -1 if none */
+  double radius;                  /* (3 V / 4 pi)^(1/3), V = number of sites with rho^r > rho^b */
+  int64_t droplet_sites;          /* V */
+  int32_t status;                 /* SC_OK, SC_ENONFINITE or SC_ESINKNEG */
+  int32_t reserved;
+} sc_diag;
+
+typedef struct sc_lbm sc_lbm;
+
+/* D3Q19 direction order used by every population array (c: [19][3]) and the weights. */
+int sc_lattice_directions(int32_t* c_host, double* w_host);
+
+/* Device bytes one lattice with these parameters needs (both population lattices,
+   diagnostics scratch). */
+int sc_lbm_required_bytes(const sc_params* p, size_t* bytes);
+
+/* Create a lattice whose device memory the library allocates (cudaMalloc) and frees
+   in sc_lbm_destroy. `stream` is a cudaStream_t (NULL = legacy default stream). */
+int sc_lbm_create(const sc_params* p, void* stream, sc_lbm** out);
+
+/* Same, on caller-owned device memory of at least sc_lbm_required_bytes() bytes,
+   256-byte aligned; the buffer must outlive the handle and is not freed by it. */
+int sc_lbm_create_ext(const sc_params* p, void* stream, void* buf_dev, size_t bytes, sc_lbm** out);
+
+void sc_lbm_destroy(sc_lbm* h);
+int sc_lbm_set_stream(sc_lbm* h, void* stream);
+int sc_lbm_sync(sc_lbm* h);
+
+/* Seeded film/droplet initial state computed on the device: rest populations
+   w_i rho from the shape plus noise, then the sink reset. Resets the step count
+   and the evaporated mass. */
+int sc_lbm_init(sc_lbm* h, const sc_init* in);
+
+/* Rest populations w_i rho from caller density fields (nx*ny*nz floats each),
+   then the sink reset. Synchronous. */
+int sc_lbm_init_fields(sc_lbm* h, const float* rho_r_host, const float* rho_b_host);
+
+/* Advance nsteps time steps (asynchronous). Each step is one fused launch:
+   stream + sink reset + densities + Psi + force + collision. */
+int sc_lbm_step(sc_lbm* h, int64_t nsteps);
+
+/* Canonical densities into caller buffers (nx*ny*nz floats each). */
+int sc_lbm_read_fields(sc_lbm* h, float* rho_r_host, float* rho_b_host);
+int sc_lbm_read_fields_device(sc_lbm* h, float* rho_r_dev, float* rho_b_dev);
+
+/* Canonical populations (2*19*nx*ny*nz doubles, converted from the storage type). */
+int sc_lbm_read_populations(sc_lbm* h, double* f_host);
+/* Replace the state by canonical populations (checkpoint restore); sink sites are
+   reset without counting evaporated mass, solid sites are ignored. Keeps the step
+   count and evaporated mass. */
+int sc_lbm_write_populations(sc_lbm* h, const double* f_host);
+/* Restore the step count and evaporated mass saved from sc_diag (checkpoint). */
+int sc_lbm_set_counters(sc_lbm* h, int64_t step, double evaporated_mass);
+
+/* FP64 diagnostics of the canonical state (synchronous). */
+int sc_lbm_diagnostics(sc_lbm* h, sc_diag* out);
+/* phi(z) = mean over non-solid (x, y) of rho^r - rho^b, nz doubles (NaN for solid planes). */
+int sc_lbm_profile(sc_lbm* h, double* phi_host);
+
+/* Kernel configuration in use: tile extents, planes per CTA, grid size. */
+int sc_lbm_launch_info(sc_lbm* h, int32_t* tile_x, int32_t* tile_y, int32_t* zchunk, int64_t* ctas);
+/* Bytes one sc_lbm_diagnostics / sc_lbm_profile call copies device-to-host. */
+int sc_lbm_diag_bytes(sc_lbm* h, size_t* bytes);
+/* Number of compiled tile shapes and their extents. */
+int sc_tile_list(int32_t* count, int32_t* tx_host, int32_t* ty_host, int32_t capacity);
+
+/* Thread-local message describing the last failure (never NULL). */
+const char* sc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SC_LBM_H */

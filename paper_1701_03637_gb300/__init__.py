@@ -1,0 +1,198 @@
+"""GB300 (sm_103a) two-component Shan-Chen D3Q19 lattice Boltzmann step with the
+fixed-density evaporation boundary of arXiv:1701.03637.
+
+``Lattice`` wraps one handle of the C ABI declared in ``include/sc_lbm.h``.
+PyTorch supplies the device memory (``sc_lbm_create_ext`` on a torch buffer) and
+the CUDA stream; every step of the method runs in the library's kernels.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _native
+from ._native import Diag, Init, Params, ScError, build, check
+
+Q = 19
+STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
+GEOMETRY = {"periodic": 0, "planar": 1, "sphere": 2}
+
+__all__ = ["Lattice", "ScError", "build", "lattice_directions", "tile_list", "required_bytes", "Q"]
+
+_PARAM_DEFAULTS = dict(tau_r=1.0, tau_b=1.0, G=3.6, rho_H=0.03, geometry=0, sink_z0=0, sink_layers=1,
+                       sphere_cx=0.0, sphere_cy=0.0, sphere_cz=0.0, R_H=0.0, wall_z0=0, wall_thickness=0,
+                       storage=0, tile=0, zchunk=0)
+_INIT_DEFAULTS = dict(shape=0, film_z=0, cx=0.0, cy=0.0, cz=0.0, radius=0.0, rho_hi=1.0, rho_lo=0.03,
+                      noise_amp=0.0, seed=0)
+
+
+def _lib():
+    return _native.load()
+
+
+def make_params(params: dict) -> Params:
+    p = dict(_PARAM_DEFAULTS)
+    p.update(params)
+    if isinstance(p.get("storage"), str):
+        p["storage"] = STORAGE[p["storage"]]
+    if isinstance(p.get("geometry"), str):
+        p["geometry"] = GEOMETRY[p["geometry"]]
+    return Params(**{k: p[k] for k, _ in Params._fields_})
+
+
+def make_init(init: dict) -> Init:
+    i = dict(_INIT_DEFAULTS)
+    i.update(init)
+    return Init(**{k: i[k] for k, _ in Init._fields_})
+
+
+def lattice_directions():
+    c = np.zeros((Q, 3), np.int32)
+    w = np.zeros(Q, np.float64)
+    check(_lib().sc_lattice_directions(c.ctypes.data, w.ctypes.data))
+    return c, w
+
+
+def tile_list():
+    n = C.c_int32()
+    tx = np.zeros(16, np.int32)
+    ty = np.zeros(16, np.int32)
+    check(_lib().sc_tile_list(C.byref(n), tx.ctypes.data, ty.ctypes.data, 16))
+    return [(int(tx[k]), int(ty[k])) for k in range(n.value)]
+
+
+def required_bytes(params: dict) -> int:
+    b = C.c_size_t()
+    check(_lib().sc_lbm_required_bytes(C.byref(make_params(params)), C.byref(b)))
+    return int(b.value)
+
+
+def _current_stream_handle(device):
+    import torch
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+class Lattice:
+    """One lattice on the current CUDA device.
+
+    ``params``: dict with the fields of ``sc_params`` (``nx, ny, nz`` required).
+    Device memory is a torch uint8 tensor lent to ``sc_lbm_create_ext`` (it must
+    outlive the handle, which this object guarantees); the stream is torch's
+    current stream unless ``stream`` (a ``torch.cuda.Stream``) is given.
+    """
+
+    def __init__(self, params: dict, device=None, stream=None):
+        import torch
+        self.torch = torch
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self._p = make_params(params)
+        self.params = {k: getattr(self._p, k) for k, _ in Params._fields_}
+        self.nx, self.ny, self.nz = self._p.nx, self._p.ny, self._p.nz
+        self.n = self.nx * self.ny * self.nz
+        self.shape = (self.nz, self.ny, self.nx)
+        nbytes = required_bytes(self.params)
+        with torch.cuda.device(self.device):
+            self._mem = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+            base = self._mem.data_ptr()
+            aligned = (base + 255) & ~255
+            self.stream = stream or torch.cuda.current_stream(self.device)
+            h = C.c_void_p()
+            check(_lib().sc_lbm_create_ext(C.byref(self._p), C.c_void_p(self.stream.cuda_stream),
+                                           C.c_void_p(aligned), C.c_size_t(nbytes), C.byref(h)))
+        self._h = h
+
+    # ------------------------------------------------------------ lifecycle
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            _lib().sc_lbm_destroy(h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_stream(self, stream):
+        self.stream = stream
+        check(_lib().sc_lbm_set_stream(self._h, C.c_void_p(stream.cuda_stream)))
+
+    def sync(self):
+        check(_lib().sc_lbm_sync(self._h))
+
+    # ------------------------------------------------------------ state
+    def init(self, init: dict) -> None:
+        check(_lib().sc_lbm_init(self._h, C.byref(make_init(init))))
+
+    def init_fields(self, rho_r, rho_b) -> None:
+        rr = np.ascontiguousarray(rho_r, np.float32).reshape(-1)
+        rb = np.ascontiguousarray(rho_b, np.float32).reshape(-1)
+        assert rr.size == self.n and rb.size == self.n
+        check(_lib().sc_lbm_init_fields(self._h, rr.ctypes.data, rb.ctypes.data))
+
+    def step(self, n: int = 1) -> None:
+        check(_lib().sc_lbm_step(self._h, int(n)))
+
+    def read_fields(self):
+        rr = np.empty(self.n, np.float32)
+        rb = np.empty(self.n, np.float32)
+        check(_lib().sc_lbm_read_fields(self._h, rr.ctypes.data, rb.ctypes.data))
+        return rr.reshape(self.shape), rb.reshape(self.shape)
+
+    def read_fields_into(self, rr_host, rb_host) -> None:
+        """Canonical densities into caller host buffers (numpy or pinned torch CPU tensors)."""
+        pr = rr_host.data_ptr() if hasattr(rr_host, "data_ptr") else rr_host.ctypes.data
+        pb = rb_host.data_ptr() if hasattr(rb_host, "data_ptr") else rb_host.ctypes.data
+        check(_lib().sc_lbm_read_fields(self._h, pr, pb))
+
+    def init_fields_from(self, rr_host, rb_host) -> None:
+        pr = rr_host.data_ptr() if hasattr(rr_host, "data_ptr") else rr_host.ctypes.data
+        pb = rb_host.data_ptr() if hasattr(rb_host, "data_ptr") else rb_host.ctypes.data
+        check(_lib().sc_lbm_init_fields(self._h, pr, pb))
+
+    def read_fields_device(self, out=None):
+        torch = self.torch
+        if out is None:
+            out = torch.empty((2, *self.shape), dtype=torch.float32, device=self.device)
+        check(_lib().sc_lbm_read_fields_device(self._h, C.c_void_p(out[0].data_ptr()),
+                                               C.c_void_p(out[1].data_ptr())))
+        return out
+
+    def read_populations(self) -> np.ndarray:
+        f = np.empty(2 * Q * self.n, np.float64)
+        check(_lib().sc_lbm_read_populations(self._h, f.ctypes.data))
+        return f.reshape(2, Q, *self.shape)
+
+    def write_populations(self, f) -> None:
+        f = np.ascontiguousarray(f, np.float64).reshape(-1)
+        assert f.size == 2 * Q * self.n
+        check(_lib().sc_lbm_write_populations(self._h, f.ctypes.data))
+
+    def set_counters(self, step: int, evaporated_mass: float) -> None:
+        check(_lib().sc_lbm_set_counters(self._h, int(step), float(evaporated_mass)))
+
+    def diagnostics(self) -> dict:
+        d = Diag()
+        check(_lib().sc_lbm_diagnostics(self._h, C.byref(d)))
+        return {k: getattr(d, k) for k, _ in Diag._fields_ if k != "reserved"}
+
+    def profile(self) -> np.ndarray:
+        out = np.empty(self.nz, np.float64)
+        check(_lib().sc_lbm_profile(self._h, out.ctypes.data))
+        return out
+
+    def diag_bytes(self) -> int:
+        b = C.c_size_t()
+        check(_lib().sc_lbm_diag_bytes(self._h, C.byref(b)))
+        return int(b.value)
+
+    def launch_info(self) -> dict:
+        tx, ty, zc, n = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int64()
+        check(_lib().sc_lbm_launch_info(self._h, C.byref(tx), C.byref(ty), C.byref(zc), C.byref(n)))
+        return dict(tile_x=tx.value, tile_y=ty.value, zchunk=zc.value, ctas=n.value)

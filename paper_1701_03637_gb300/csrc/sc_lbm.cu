@@ -1,0 +1,776 @@
+// sc_lbm: C ABI and launches for the two-component Shan-Chen D3Q19 evaporation
+// step on sm_103a (arXiv:1701.03637, Sec. II). See include/sc_lbm.h for the
+// contract of every entry point.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <type_traits>
+#include <vector>
+
+#include "sc_kernels.cuh"
+#include "sc_lbm.h"
+
+using namespace sclbm;
+
+namespace {
+
+thread_local char g_err[512] = "no error";
+
+int fail(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+#define CK(call)                                                                                  \
+  do {                                                                                            \
+    cudaError_t e_ = (call);                                                                      \
+    if (e_ != cudaSuccess) return fail(SC_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+constexpr int kNumTiles = 4;
+constexpr int kTileX[kNumTiles] = {32, 32, 16, 8};
+constexpr int kTileY[kNumTiles] = {8, 4, 8, 4};
+
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+// ------------------------------------------------------------------ kernels
+
+template <int TX, int TY, class S>
+__global__ void __launch_bounds__(TX * TY, 2)
+    k_step(const LatDev L, const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
+           double* __restrict__ evap_cum, int zchunk) {
+  using TileT = Tile<TX, TY, S>;
+  __shared__ typename TileT::Smem sm;
+  TileT t(L, sm, src, dst, blockIdx.x, blockIdx.y);
+  const int zb = blockIdx.z * zchunk;
+  const int ze = min(zb + zchunk, L.nz);
+  t.run(zb, ze);
+  if (L.geometry != 0) {
+    const double e = t.block_evap();
+    if (threadIdx.x == 0) {
+      const long long slot = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+      evap_cum[slot] += e;
+    }
+  }
+}
+
+// Canonical state of every site (pull + sink), as densities and/or populations
+// for sites [s0, s1).
+template <class S>
+__global__ void k_canonical(const LatDev L, const typename S::T* __restrict__ src, long long s0, long long s1,
+                            float* __restrict__ rho_out, long long rho_stride, float* __restrict__ f_out,
+                            long long f_stride) {
+  for (long long s = s0 + blockIdx.x * (long long)blockDim.x + threadIdx.x; s < s1;
+       s += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(s % L.nx), y = (int)((s / L.nx) % L.ny), z = (int)(s / L.nxny);
+    const int cls = site_class(L, x, y, z);
+    float fr[Q], fb[Q], rr = 0.f, rb = 0.f;
+    if (cls == SOLID) {
+#pragma unroll
+      for (int i = 0; i < Q; ++i) fr[i] = fb[i] = 0.f;
+    } else {
+      const PullIdx P(L, x, y, z);
+      pull_full<S>(L, src, P, fr, fb);
+      rr = sum19(fr);
+      rb = sum19(fb);
+      if (cls == SINK) {
+        sink_densities(L, rr, rb);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) { fr[i] = wgt(i) * rr; fb[i] = wgt(i) * rb; }
+      }
+    }
+    const long long o = s - s0;
+    if (rho_out) { rho_out[o] = rr; rho_out[rho_stride + o] = rb; }
+    if (f_out) {
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        f_out[(long long)i * f_stride + o] = fr[i];
+        f_out[(long long)(Q + i) * f_stride + o] = fb[i];
+      }
+    }
+  }
+}
+
+// FP64 plane diagnostics: per (plane, split) mass_r, mass_b, sum(rho_r - rho_b),
+// pending evaporation of the canonical state, sites with rho_r > rho_b, flags.
+constexpr int kDiagFields = 8;
+constexpr int kDiagThreads = 256;
+
+template <class S>
+__global__ void __launch_bounds__(kDiagThreads) k_diag(const LatDev L, const typename S::T* __restrict__ src,
+                                                       int nsplit, double* __restrict__ part) {
+  const int z = blockIdx.x, k = blockIdx.y;
+  const int per = (L.nxny + nsplit - 1) / nsplit;
+  const int b = k * per, e = min(b + per, L.nxny);
+  // mass_r, mass_b, sum(rho_r - rho_b), pending evaporation, count(rho_r > rho_b),
+  // non-finite flag, negative-complement flag
+  constexpr int NF = 7;
+  double acc[NF] = {0, 0, 0, 0, 0, 0, 0};
+  if (!solid_z(L, z)) {
+    for (int q = b + threadIdx.x; q < e; q += blockDim.x) {
+      const int x = q % L.nx, y = q / L.nx;
+      const int cls = site_class(L, x, y, z);
+      const PullIdx P(L, x, y, z);
+      float rr, rb;
+      pull_sums<S>(L, src, P, rr, rb);
+      if (cls == SINK) {
+        acc[3] += (double)rr - L.rhoH_d;
+        sink_densities(L, rr, rb);
+        if (rb < 0.0f) acc[6] = 1.0;
+      }
+      if (!isfinite(rr) || !isfinite(rb)) acc[5] = 1.0;
+      acc[0] += rr;
+      acc[1] += rb;
+      acc[2] += (double)rr - (double)rb;
+      acc[4] += rr > rb ? 1.0 : 0.0;
+    }
+  }
+  __shared__ double red[kDiagThreads / 32][NF];
+#pragma unroll
+  for (int j = 0; j < NF; ++j) {
+    double v = acc[j];
+    for (int o = 16; o > 0; o >>= 1) {
+      const double w = __shfl_down_sync(0xffffffffu, v, o);
+      v = (j >= 5) ? fmax(v, w) : v + w;
+    }
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][j] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < NF) {
+    const int j = threadIdx.x;
+    double t = 0.0;
+    for (int w = 0; w < kDiagThreads / 32; ++w) t = (j >= 5) ? fmax(t, red[w][j]) : t + red[w][j];
+    part[((long long)z * nsplit + k) * kDiagFields + j] = t;
+  }
+}
+
+// Initial / restored state: canonical populations of sites [s0, s1) from
+// (mode 0) an FP32 population slab, (mode 1) density fields, (mode 2) the seeded
+// film/droplet shape. Sinks are reset (evaporated mass not counted) and the
+// values are written to the slot the next pull reads them from.
+struct ShapeDev {
+  int shape, film_z;
+  double cx, cy, cz, R2, hi, lo, amp;
+  unsigned long long seed;
+};
+
+// SplitMix64 (Steele, Lea & Flood 2014): output k of the generator seeded with
+// `seed` is the finaliser applied to seed + k * 0x9E3779B97F4A7C15.
+__device__ __forceinline__ unsigned long long splitmix64_at(unsigned long long seed, unsigned long long k) {
+  unsigned long long z = seed + k * 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+template <class S>
+__global__ void k_load(const LatDev L, typename S::T* __restrict__ dst, long long s0, long long s1, int mode,
+                       const float* __restrict__ f_in, long long f_stride, const float* __restrict__ rho_in,
+                       long long rho_stride, const ShapeDev sh, long long nsites) {
+  for (long long s = s0 + blockIdx.x * (long long)blockDim.x + threadIdx.x; s < s1;
+       s += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(s % L.nx), y = (int)((s / L.nx) % L.ny), z = (int)(s / L.nxny);
+    const int cls = site_class(L, x, y, z);
+    if (cls == SOLID) continue;
+    const long long o = s - s0;
+    float fr[Q], fb[Q];
+    if (mode == 0) {
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        fr[i] = f_in[(long long)i * f_stride + o];
+        fb[i] = f_in[(long long)(Q + i) * f_stride + o];
+      }
+    } else if (mode == 1) {
+      const float r = rho_in[o], b = rho_in[rho_stride + o];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) { fr[i] = wgt(i) * r; fb[i] = wgt(i) * b; }
+    } else {
+      bool rich;
+      if (sh.shape == 0) {
+        rich = z < sh.film_z;
+      } else {
+        const double dx = (double)x - sh.cx, dy = (double)y - sh.cy, dz = (double)z - sh.cz;
+        rich = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)) < sh.R2;
+      }
+      const double ur = (double)(splitmix64_at(sh.seed, 1ULL + (unsigned long long)s) >> 11) * 0x1.0p-53;
+      const double ub =
+          (double)(splitmix64_at(sh.seed, 1ULL + (unsigned long long)nsites + (unsigned long long)s) >> 11) * 0x1.0p-53;
+      const double r = (rich ? sh.hi : sh.lo) + __dmul_rn(sh.amp, __dadd_rn(2.0 * ur, -1.0));
+      const double b = (rich ? sh.lo : sh.hi) + __dmul_rn(sh.amp, __dadd_rn(2.0 * ub, -1.0));
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        fr[i] = (float)__dmul_rn(wgt_d(i), r);
+        fb[i] = (float)__dmul_rn(wgt_d(i), b);
+      }
+    }
+    if (cls == SINK) {
+      float rr = sum19(fr), rb = sum19(fb);
+      sink_densities(L, rr, rb);
+#pragma unroll
+      for (int i = 0; i < Q; ++i) { fr[i] = wgt(i) * rr; fb[i] = wgt(i) * rb; }
+    }
+    // inverse of the pull: f_i(x) is read from x - e_i, or from (x, opp(i)) when
+    // x - e_i is solid.
+    const PullIdx P(L, x, y, z);
+    const long long cstride = (long long)Q * L.np;
+    Unroll<0, Q>::run([&](auto ic) {
+      constexpr int I = decltype(ic)::value;
+      int idx, d;
+      P.template at<I>(idx, d);
+      typename S::T* p = dst + (long long)d * L.np + idx;
+      S::st(p, fr[I], wgt(I));
+      S::st(p + cstride, fb[I], wgt(I));
+    });
+  }
+}
+
+// ------------------------------------------------------------------ launch tables
+
+using StepFn = void (*)(const LatDev, const void*, void*, double*, int);
+
+template <int TX, int TY, class S>
+cudaError_t launch_step(const LatDev& L, const void* src, void* dst, double* evap, int zchunk, dim3 grid,
+                        cudaStream_t st) {
+  k_step<TX, TY, S><<<grid, TX * TY, 0, st>>>(L, (const typename S::T*)src, (typename S::T*)dst, evap, zchunk);
+  return cudaGetLastError();
+}
+
+using LaunchFn = cudaError_t (*)(const LatDev&, const void*, void*, double*, int, dim3, cudaStream_t);
+
+template <class S>
+LaunchFn pick_step(int tile) {
+  switch (tile) {
+    case 0: return &launch_step<32, 8, S>;
+    case 1: return &launch_step<32, 4, S>;
+    case 2: return &launch_step<16, 8, S>;
+    default: return &launch_step<8, 4, S>;
+  }
+}
+
+LaunchFn step_fn(int storage, int tile) {
+  switch (storage) {
+    case SC_STORAGE_F16: return pick_step<StF16>(tile);
+    case SC_STORAGE_BF16: return pick_step<StBF16>(tile);
+    default: return pick_step<StF32>(tile);
+  }
+}
+
+size_t elem_size(int storage) { return storage == SC_STORAGE_F32 ? 4 : 2; }
+
+int validate(const sc_params* p) {
+  if (!p) return fail(SC_EINVAL, "params is NULL");
+  if (p->nx < 1 || p->ny < 1 || p->nz < 1) return fail(SC_EINVAL, "lattice extents must be >= 1");
+  if ((long long)p->nx * p->ny * p->nz > (1LL << 31) - 4096)
+    return fail(SC_EINVAL, "lattice too large: nx*ny*nz must stay below 2^31");
+  if (!(p->tau_r > 0.5) || !(p->tau_b > 0.5)) return fail(SC_EINVAL, "tau must exceed 1/2");
+  if (!std::isfinite(p->G) || !std::isfinite(p->rho_H)) return fail(SC_EINVAL, "G and rho_H must be finite");
+  if (p->geometry < 0 || p->geometry > 2) return fail(SC_EINVAL, "unknown geometry %d", p->geometry);
+  if (p->geometry == 1 && (p->sink_layers < 1 || p->sink_layers > p->nz))
+    return fail(SC_EINVAL, "sink_layers must be in [1, nz]");
+  if (p->geometry == 2 && !(p->R_H > 0)) return fail(SC_EINVAL, "R_H must be > 0");
+  if (p->wall_thickness < 0 || (p->wall_thickness > 0 && (p->wall_z0 < 0 || p->wall_z0 + p->wall_thickness > p->nz)))
+    return fail(SC_EINVAL, "wall slab must lie inside [0, nz)");
+  if (p->storage < 0 || p->storage > 2) return fail(SC_EINVAL, "unknown storage %d", p->storage);
+  if (p->tile < 0 || p->tile > kNumTiles) return fail(SC_EINVAL, "tile index out of range");
+  if (p->zchunk < 0) return fail(SC_EINVAL, "zchunk must be >= 0");
+  return SC_OK;
+}
+
+struct Layout {
+  int tile, tx, ty, zchunk;
+  long long np, nsites;
+  dim3 grid;
+  long long nctas;
+  int diag_nsplit;
+  size_t off_pop[2], off_stage, off_evap, off_diag, total;
+};
+
+int auto_tile(const sc_params* p) {
+  if (p->nx >= 32) return p->ny >= 8 ? 0 : 1;
+  if (p->nx >= 16) return 2;
+  return 3;
+}
+
+Layout make_layout(const sc_params* p) {
+  Layout l{};
+  l.tile = p->tile > 0 ? p->tile - 1 : auto_tile(p);
+  l.tx = kTileX[l.tile];
+  l.ty = kTileY[l.tile];
+  l.nsites = (long long)p->nx * p->ny * p->nz;
+  l.np = (l.nsites + 127) / 128 * 128;
+  const long long cols = (long long)((p->nx + l.tx - 1) / l.tx) * ((p->ny + l.ty - 1) / l.ty);
+  int zc = p->zchunk;
+  if (zc <= 0) {
+    const long long target = 4LL * 152;  // about two waves at two CTAs per SM
+    long long nch = (target + cols - 1) / cols;
+    nch = std::max(1LL, std::min<long long>(nch, p->nz));
+    zc = (int)((p->nz + nch - 1) / nch);
+  }
+  zc = std::min(zc, p->nz);
+  l.zchunk = zc;
+  l.grid = dim3((p->nx + l.tx - 1) / l.tx, (p->ny + l.ty - 1) / l.ty, (p->nz + zc - 1) / zc);
+  l.nctas = (long long)l.grid.x * l.grid.y * l.grid.z;
+  const long long per_plane = (long long)p->nx * p->ny;
+  l.diag_nsplit = (int)std::max(1LL, std::min<long long>((4LL * 152 + p->nz - 1) / p->nz, (per_plane + 1023) / 1024));
+  const size_t pop = align256((size_t)2 * Q * l.np * elem_size(p->storage));
+  size_t off = 0;
+  l.off_pop[0] = off; off += pop;
+  l.off_pop[1] = off; off += pop;
+  l.off_stage = off; off += align256((size_t)2 * l.np * sizeof(float));
+  l.off_evap = off; off += align256((size_t)l.nctas * sizeof(double));
+  l.off_diag = off; off += align256((size_t)p->nz * l.diag_nsplit * kDiagFields * sizeof(double));
+  l.total = off;
+  return l;
+}
+
+LatDev make_dev(const sc_params* p, const Layout& l) {
+  LatDev L{};
+  L.nx = p->nx; L.ny = p->ny; L.nz = p->nz; L.nxny = p->nx * p->ny;
+  L.np = l.np;
+  L.tau[0] = (float)p->tau_r; L.tau[1] = (float)p->tau_b;
+  L.omega[0] = (float)(1.0 / p->tau_r); L.omega[1] = (float)(1.0 / p->tau_b);
+  L.G = (float)p->G;
+  L.rhoH = (float)p->rho_H;
+  L.rhoH_d = (double)(float)p->rho_H;
+  L.geometry = p->geometry;
+  L.sink_z0 = p->sink_z0; L.sink_layers = p->sink_layers;
+  L.scx = p->sphere_cx; L.scy = p->sphere_cy; L.scz = p->sphere_cz; L.RH2 = p->R_H * p->R_H;
+  if (p->wall_thickness > 0) { L.wall_z0 = p->wall_z0; L.wall_z1 = p->wall_z0 + p->wall_thickness; }
+  else { L.wall_z0 = 0; L.wall_z1 = 0; }
+  return L;
+}
+
+}  // namespace
+
+struct sc_lbm {
+  sc_params p;
+  Layout lay;
+  LatDev L;
+  cudaStream_t stream;
+  char* base;
+  bool owns;
+  int cur;  // buffer holding the current pre-stream state
+  int64_t step;
+  double evap_offset;  // evaporated mass restored by sc_lbm_set_counters
+  double* h_diag;      // pinned
+  double* h_evap;      // pinned
+  cudaGraphExec_t graph;
+  int graph_len;
+  int graph_cur;
+  void* pop(int k) const { return base + lay.off_pop[k]; }
+  float* stage() const { return (float*)(base + lay.off_stage); }
+  double* evap() const { return (double*)(base + lay.off_evap); }
+  double* diag() const { return (double*)(base + lay.off_diag); }
+};
+
+namespace {
+
+int launch_one(sc_lbm* h, cudaStream_t st) {
+  const int src = h->cur, dst = 1 - h->cur;
+  cudaError_t e = step_fn(h->p.storage, h->lay.tile)(h->L, h->pop(src), h->pop(dst), h->evap(), h->lay.zchunk,
+                                                      h->lay.grid, st);
+  if (e != cudaSuccess) return fail(SC_ECUDA, "step launch failed: %s", cudaGetErrorString(e));
+  h->cur = dst;
+  return SC_OK;
+}
+
+template <class S>
+int launch_canonical(sc_lbm* h, long long s0, long long s1, float* rho, long long rs, float* f, long long fs) {
+  const long long n = s1 - s0;
+  const int threads = 256;
+  const long long blocks = std::min<long long>((n + threads - 1) / threads, 152LL * 16);
+  k_canonical<S><<<(unsigned)std::max(1LL, blocks), threads, 0, h->stream>>>(
+      h->L, (const typename S::T*)h->pop(h->cur), s0, s1, rho, rs, f, fs);
+  CK(cudaGetLastError());
+  return SC_OK;
+}
+
+int canonical(sc_lbm* h, long long s0, long long s1, float* rho, long long rs, float* f, long long fs) {
+  switch (h->p.storage) {
+    case SC_STORAGE_F16: return launch_canonical<StF16>(h, s0, s1, rho, rs, f, fs);
+    case SC_STORAGE_BF16: return launch_canonical<StBF16>(h, s0, s1, rho, rs, f, fs);
+    default: return launch_canonical<StF32>(h, s0, s1, rho, rs, f, fs);
+  }
+}
+
+template <class S>
+int launch_load(sc_lbm* h, long long s0, long long s1, int mode, const float* f, long long fs, const float* rho,
+                long long rs, const ShapeDev& sh) {
+  const long long n = s1 - s0;
+  const int threads = 256;
+  const long long blocks = std::min<long long>((n + threads - 1) / threads, 152LL * 16);
+  // the pull reads the current buffer, so the load writes it
+  k_load<S><<<(unsigned)std::max(1LL, blocks), threads, 0, h->stream>>>(
+      h->L, (typename S::T*)h->pop(h->cur), s0, s1, mode, f, fs, rho, rs, sh, h->lay.nsites);
+  CK(cudaGetLastError());
+  return SC_OK;
+}
+
+int load(sc_lbm* h, long long s0, long long s1, int mode, const float* f, long long fs, const float* rho,
+         long long rs, const ShapeDev& sh) {
+  switch (h->p.storage) {
+    case SC_STORAGE_F16: return launch_load<StF16>(h, s0, s1, mode, f, fs, rho, rs, sh);
+    case SC_STORAGE_BF16: return launch_load<StBF16>(h, s0, s1, mode, f, fs, rho, rs, sh);
+    default: return launch_load<StF32>(h, s0, s1, mode, f, fs, rho, rs, sh);
+  }
+}
+
+template <class S>
+int launch_diag(sc_lbm* h) {
+  dim3 grid(h->p.nz, h->lay.diag_nsplit);
+  k_diag<S><<<grid, kDiagThreads, 0, h->stream>>>(h->L, (const typename S::T*)h->pop(h->cur), h->lay.diag_nsplit,
+                                                  h->diag());
+  CK(cudaGetLastError());
+  return SC_OK;
+}
+
+int reset_counters(sc_lbm* h) {
+  CK(cudaMemsetAsync(h->evap(), 0, sizeof(double) * h->lay.nctas, h->stream));
+  h->step = 0;
+  h->evap_offset = 0.0;
+  return SC_OK;
+}
+
+// Sites per slab so a slab's 2*19 FP32 populations fit the 2*np-float staging area.
+long long slab_sites(const sc_lbm* h) { return std::max<long long>(1, (2 * h->lay.np) / (2 * Q)); }
+
+}  // namespace
+
+extern "C" {
+
+const char* sc_last_error(void) { return g_err; }
+
+int sc_lattice_directions(int32_t* c, double* w) {
+  for (int i = 0; i < Q; ++i) {
+    if (c) { c[3 * i] = dir_x(i); c[3 * i + 1] = dir_y(i); c[3 * i + 2] = dir_z(i); }
+    if (w) w[i] = wgt_d(i);
+  }
+  return SC_OK;
+}
+
+int sc_tile_list(int32_t* count, int32_t* tx, int32_t* ty, int32_t capacity) {
+  if (count) *count = kNumTiles;
+  for (int k = 0; k < kNumTiles && k < capacity; ++k) {
+    if (tx) tx[k] = kTileX[k];
+    if (ty) ty[k] = kTileY[k];
+  }
+  return SC_OK;
+}
+
+int sc_lbm_required_bytes(const sc_params* p, size_t* bytes) {
+  int rc = validate(p);
+  if (rc) return rc;
+  if (!bytes) return fail(SC_EINVAL, "bytes is NULL");
+  *bytes = make_layout(p).total;
+  return SC_OK;
+}
+
+static int create_common(const sc_params* p, void* stream, void* buf, size_t bytes, bool owns, sc_lbm** out) {
+  sc_lbm* h = new (std::nothrow) sc_lbm();
+  if (!h) return fail(SC_ENOMEM, "host allocation failed");
+  h->p = *p;
+  h->lay = make_layout(p);
+  h->L = make_dev(p, h->lay);
+  h->stream = (cudaStream_t)stream;
+  h->base = (char*)buf;
+  h->owns = owns;
+  h->cur = 0;
+  h->graph = nullptr;
+  h->graph_len = 0;
+  h->graph_cur = 0;
+  cudaError_t e = cudaMallocHost((void**)&h->h_diag, sizeof(double) * p->nz * h->lay.diag_nsplit * kDiagFields);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&h->h_evap, sizeof(double) * h->lay.nctas);
+  if (e != cudaSuccess) {
+    if (h->h_diag) cudaFreeHost(h->h_diag);
+    if (owns) cudaFree(buf);
+    delete h;
+    return fail(SC_ENOMEM, "pinned host allocation failed: %s", cudaGetErrorString(e));
+  }
+  (void)bytes;
+  int rc = reset_counters(h);
+  if (rc) { sc_lbm_destroy(h); return rc; }
+  *out = h;
+  return SC_OK;
+}
+
+int sc_lbm_create(const sc_params* p, void* stream, sc_lbm** out) {
+  int rc = validate(p);
+  if (rc) return rc;
+  if (!out) return fail(SC_EINVAL, "out is NULL");
+  const Layout l = make_layout(p);
+  void* buf = nullptr;
+  cudaError_t e = cudaMalloc(&buf, l.total);
+  if (e != cudaSuccess) return fail(SC_ENOMEM, "cudaMalloc(%zu) failed: %s", l.total, cudaGetErrorString(e));
+  return create_common(p, stream, buf, l.total, true, out);
+}
+
+int sc_lbm_create_ext(const sc_params* p, void* stream, void* buf, size_t bytes, sc_lbm** out) {
+  int rc = validate(p);
+  if (rc) return rc;
+  if (!out || !buf) return fail(SC_EINVAL, "NULL argument");
+  if (((uintptr_t)buf & 255) != 0) return fail(SC_EINVAL, "device buffer must be 256-byte aligned");
+  const Layout l = make_layout(p);
+  if (bytes < l.total) return fail(SC_ENOMEM, "device buffer has %zu bytes, needs %zu", bytes, l.total);
+  return create_common(p, stream, buf, bytes, false, out);
+}
+
+void sc_lbm_destroy(sc_lbm* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  if (h->h_diag) cudaFreeHost(h->h_diag);
+  if (h->h_evap) cudaFreeHost(h->h_evap);
+  if (h->owns && h->base) cudaFree(h->base);
+  delete h;
+}
+
+int sc_lbm_set_stream(sc_lbm* h, void* stream) {
+  if (!h) return fail(SC_EINVAL, "NULL handle");
+  h->stream = (cudaStream_t)stream;
+  return SC_OK;
+}
+
+int sc_lbm_sync(sc_lbm* h) {
+  if (!h) return fail(SC_EINVAL, "NULL handle");
+  CK(cudaStreamSynchronize(h->stream));
+  return SC_OK;
+}
+
+int sc_lbm_init(sc_lbm* h, const sc_init* in) {
+  if (!h || !in) return fail(SC_EINVAL, "NULL argument");
+  if (in->shape < 0 || in->shape > 1) return fail(SC_EINVAL, "unknown shape %d", in->shape);
+  if (!std::isfinite(in->rho_hi) || !std::isfinite(in->rho_lo) || !std::isfinite(in->noise_amp))
+    return fail(SC_EINVAL, "densities must be finite");
+  ShapeDev sh{};
+  sh.shape = in->shape; sh.film_z = in->film_z;
+  sh.cx = in->cx; sh.cy = in->cy; sh.cz = in->cz; sh.R2 = in->radius * in->radius;
+  sh.hi = in->rho_hi; sh.lo = in->rho_lo; sh.amp = in->noise_amp; sh.seed = in->seed;
+  int rc = load(h, 0, h->lay.nsites, 2, nullptr, 0, nullptr, 0, sh);
+  if (rc) return rc;
+  return reset_counters(h);
+}
+
+int sc_lbm_init_fields(sc_lbm* h, const float* rr, const float* rb) {
+  if (!h || !rr || !rb) return fail(SC_EINVAL, "NULL argument");
+  const long long n = h->lay.nsites;
+  float* st = h->stage();
+  CK(cudaMemcpyAsync(st, rr, sizeof(float) * n, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(st + h->lay.np, rb, sizeof(float) * n, cudaMemcpyHostToDevice, h->stream));
+  ShapeDev sh{};
+  int rc = load(h, 0, n, 1, nullptr, 0, st, h->lay.np, sh);
+  if (rc) return rc;
+  rc = reset_counters(h);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(h->stream));
+  return SC_OK;
+}
+
+static int ensure_graph(sc_lbm* h) {
+  if (h->graph) return SC_OK;
+  // enough launches per replay that launch overhead is amortised on small lattices
+  const long long n = h->lay.nsites;
+  int len = (int)std::min<long long>(64, std::max<long long>(2, (1LL << 21) / std::max<long long>(n, 1)));
+  len += len & 1;
+  cudaStream_t cs;
+  CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  const int saved = h->cur;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  int rc = SC_OK;
+  if (e == cudaSuccess) {
+    for (int k = 0; k < len && rc == SC_OK; ++k) rc = launch_one(h, cs);
+    e = cudaStreamEndCapture(cs, &g);
+  }
+  h->cur = saved;
+  cudaStreamDestroy(cs);
+  if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+  if (e != cudaSuccess) return fail(SC_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&h->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) { h->graph = nullptr; return fail(SC_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e)); }
+  h->graph_len = len;
+  h->graph_cur = saved;
+  return SC_OK;
+}
+
+int sc_lbm_step(sc_lbm* h, int64_t nsteps) {
+  if (!h) return fail(SC_EINVAL, "NULL handle");
+  if (nsteps < 0) return fail(SC_EINVAL, "nsteps must be >= 0");
+  int64_t left = nsteps;
+  if (left >= 4) {
+    int rc = ensure_graph(h);
+    if (rc) return rc;
+  }
+  while (left > 0) {
+    if (h->graph && left >= h->graph_len && h->cur == h->graph_cur) {
+      CK(cudaGraphLaunch(h->graph, h->stream));
+      left -= h->graph_len;  // graph_len is even: the buffer parity is unchanged
+    } else {
+      int rc = launch_one(h, h->stream);
+      if (rc) return rc;
+      left -= 1;
+    }
+  }
+  h->step += nsteps;
+  return SC_OK;
+}
+
+int sc_lbm_read_fields_device(sc_lbm* h, float* rr, float* rb) {
+  if (!h || !rr || !rb) return fail(SC_EINVAL, "NULL argument");
+  int rc = canonical(h, 0, h->lay.nsites, h->stage(), h->lay.np, nullptr, 0);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(rr, h->stage(), sizeof(float) * h->lay.nsites, cudaMemcpyDeviceToDevice, h->stream));
+  CK(cudaMemcpyAsync(rb, h->stage() + h->lay.np, sizeof(float) * h->lay.nsites, cudaMemcpyDeviceToDevice,
+                     h->stream));
+  return SC_OK;
+}
+
+int sc_lbm_read_fields(sc_lbm* h, float* rr, float* rb) {
+  if (!h || !rr || !rb) return fail(SC_EINVAL, "NULL argument");
+  int rc = canonical(h, 0, h->lay.nsites, h->stage(), h->lay.np, nullptr, 0);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(rr, h->stage(), sizeof(float) * h->lay.nsites, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(rb, h->stage() + h->lay.np, sizeof(float) * h->lay.nsites, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return SC_OK;
+}
+
+int sc_lbm_read_populations(sc_lbm* h, double* f) {
+  if (!h || !f) return fail(SC_EINVAL, "NULL argument");
+  const long long n = h->lay.nsites, slab = slab_sites(h);
+  std::vector<float> tmp;
+  try { tmp.resize((size_t)2 * Q * slab); } catch (...) { return fail(SC_ENOMEM, "host allocation failed"); }
+  for (long long s0 = 0; s0 < n; s0 += slab) {
+    const long long s1 = std::min(n, s0 + slab), m = s1 - s0;
+    int rc = canonical(h, s0, s1, nullptr, 0, h->stage(), m);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(tmp.data(), h->stage(), sizeof(float) * 2 * Q * m, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    for (int k = 0; k < 2 * Q; ++k)
+      for (long long o = 0; o < m; ++o) f[(long long)k * n + s0 + o] = (double)tmp[(size_t)k * m + o];
+  }
+  return SC_OK;
+}
+
+int sc_lbm_write_populations(sc_lbm* h, const double* f) {
+  if (!h || !f) return fail(SC_EINVAL, "NULL argument");
+  const long long n = h->lay.nsites, slab = slab_sites(h);
+  std::vector<float> tmp;
+  try { tmp.resize((size_t)2 * Q * slab); } catch (...) { return fail(SC_ENOMEM, "host allocation failed"); }
+  ShapeDev sh{};
+  for (long long s0 = 0; s0 < n; s0 += slab) {
+    const long long s1 = std::min(n, s0 + slab), m = s1 - s0;
+    for (int k = 0; k < 2 * Q; ++k)
+      for (long long o = 0; o < m; ++o) tmp[(size_t)k * m + o] = (float)f[(long long)k * n + s0 + o];
+    CK(cudaMemcpyAsync(h->stage(), tmp.data(), sizeof(float) * 2 * Q * m, cudaMemcpyHostToDevice, h->stream));
+    int rc = load(h, s0, s1, 0, h->stage(), m, nullptr, 0, sh);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(h->stream));  // tmp is reused for the next slab
+  }
+  return SC_OK;
+}
+
+int sc_lbm_set_counters(sc_lbm* h, int64_t step, double evaporated) {
+  if (!h) return fail(SC_EINVAL, "NULL handle");
+  CK(cudaMemsetAsync(h->evap(), 0, sizeof(double) * h->lay.nctas, h->stream));
+  h->step = step;
+  h->evap_offset = evaporated;
+  return SC_OK;
+}
+
+static int run_diag(sc_lbm* h) {
+  int rc;
+  switch (h->p.storage) {
+    case SC_STORAGE_F16: rc = launch_diag<StF16>(h); break;
+    case SC_STORAGE_BF16: rc = launch_diag<StBF16>(h); break;
+    default: rc = launch_diag<StF32>(h);
+  }
+  if (rc) return rc;
+  const size_t nd = (size_t)h->p.nz * h->lay.diag_nsplit * kDiagFields;
+  CK(cudaMemcpyAsync(h->h_diag, h->diag(), sizeof(double) * nd, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(h->h_evap, h->evap(), sizeof(double) * h->lay.nctas, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return SC_OK;
+}
+
+int sc_lbm_profile(sc_lbm* h, double* phi) {
+  if (!h || !phi) return fail(SC_EINVAL, "NULL argument");
+  int rc = run_diag(h);
+  if (rc) return rc;
+  const int ns = h->lay.diag_nsplit;
+  for (int z = 0; z < h->p.nz; ++z) {
+    if (h->L.wall_z0 <= z && z < h->L.wall_z1) { phi[z] = NAN; continue; }
+    double acc = 0.0;
+    for (int k = 0; k < ns; ++k) acc += h->h_diag[((size_t)z * ns + k) * kDiagFields + 2];
+    phi[z] = acc / (double)h->L.nxny;
+  }
+  return SC_OK;
+}
+
+int sc_lbm_diagnostics(sc_lbm* h, sc_diag* d) {
+  if (!h || !d) return fail(SC_EINVAL, "NULL argument");
+  int rc = run_diag(h);
+  if (rc) return rc;
+  std::memset(d, 0, sizeof(*d));
+  const int nz = h->p.nz, ns = h->lay.diag_nsplit;
+  std::vector<double> phi(nz);
+  double pending = 0.0, count = 0.0, nonfinite = 0.0, sinkneg = 0.0;
+  for (int z = 0; z < nz; ++z) {
+    double pz = 0.0;
+    for (int k = 0; k < ns; ++k) {
+      const double* q = h->h_diag + ((size_t)z * ns + k) * kDiagFields;
+      d->mass_r += q[0];
+      d->mass_b += q[1];
+      pz += q[2];
+      pending += q[3];
+      count += q[4];
+      nonfinite = std::max(nonfinite, q[5]);
+      sinkneg = std::max(sinkneg, q[6]);
+    }
+    phi[z] = (h->L.wall_z0 <= z && z < h->L.wall_z1) ? NAN : pz / (double)h->L.nxny;
+  }
+  double cum = 0.0;
+  for (long long k = 0; k < h->lay.nctas; ++k) cum += h->h_evap[k];
+  d->step = h->step;
+  d->evaporated_mass = h->evap_offset + cum + pending;
+  d->flux_last = pending;
+  d->droplet_sites = (int64_t)count;
+  d->radius = std::cbrt(3.0 * count / (4.0 * M_PI));
+  const int z0 = h->L.wall_z1 > h->L.wall_z0 ? h->L.wall_z1 : 0;
+  d->interface_z = -1.0;
+  for (int z = z0; z + 1 < nz; ++z) {
+    if (std::isnan(phi[z]) || std::isnan(phi[z + 1])) continue;
+    if (phi[z] > 0.0 && phi[z + 1] <= 0.0) {
+      d->interface_z = z + phi[z] / (phi[z] - phi[z + 1]);
+      break;
+    }
+  }
+  d->status = nonfinite > 0.0 ? SC_ENONFINITE : (sinkneg > 0.0 ? SC_ESINKNEG : SC_OK);
+  if (!std::isfinite(d->mass_r) || !std::isfinite(d->mass_b)) d->status = SC_ENONFINITE;
+  return SC_OK;
+}
+
+int sc_lbm_launch_info(sc_lbm* h, int32_t* tx, int32_t* ty, int32_t* zchunk, int64_t* ctas) {
+  if (!h) return fail(SC_EINVAL, "NULL handle");
+  if (tx) *tx = h->lay.tx;
+  if (ty) *ty = h->lay.ty;
+  if (zchunk) *zchunk = h->lay.zchunk;
+  if (ctas) *ctas = h->lay.nctas;
+  return SC_OK;
+}
+
+int sc_lbm_diag_bytes(sc_lbm* h, size_t* bytes) {
+  if (!h || !bytes) return fail(SC_EINVAL, "NULL argument");
+  *bytes = sizeof(double) * ((size_t)h->p.nz * h->lay.diag_nsplit * kDiagFields + (size_t)h->lay.nctas);
+  return SC_OK;
+}
+
+}  // extern "C"

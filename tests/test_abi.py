@@ -1,0 +1,70 @@
+"""Host-only checks of the C ABI: the library builds for sm_103a, loads, exports
+every entry point include/sc_lbm.h declares, and validates arguments without
+touching a GPU."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def native():
+    from paper_1701_03637_gb300 import _native
+    _native.build()
+    return _native
+
+
+def _declared(header):
+    text = open(os.path.join(ROOT, "include", header)).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sc_\w+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol(native):
+    lib = C.CDLL(native.LIB_PATH)
+    declared = _declared("sc_lbm.h")
+    assert len(declared) >= 20
+    for name in declared:
+        assert hasattr(lib, name), name
+    # the binding declares exactly the header's entry points
+    assert set(native.declared_symbols()) == set(declared)
+
+
+def test_only_sc_symbols_exported(native):
+    import subprocess
+    out = subprocess.run(["nm", "-D", "--defined-only", native.LIB_PATH], capture_output=True, text=True).stdout
+    names = [ln.split()[-1] for ln in out.splitlines() if ln.strip()]
+    assert names and all(n.startswith("sc_") for n in names), [n for n in names if not n.startswith("sc_")][:5]
+
+
+def test_direction_table_matches_oracle_order(native, oracle_mod):
+    import paper_1701_03637_gb300 as sc
+    c, w = sc.lattice_directions()
+    oc, ow, _ = oracle_mod.tables()
+    assert np.array_equal(c, oc)
+    assert np.allclose(w, ow, rtol=0, atol=0)
+
+
+@pytest.mark.parametrize("bad", [dict(nx=0), dict(tau_r=0.5), dict(geometry=7), dict(storage=5),
+                                 dict(geometry=1, sink_layers=0), dict(wall_thickness=3, wall_z0=7),
+                                 dict(geometry=2, R_H=0.0), dict(tile=99), dict(G=float("nan"))])
+def test_invalid_params_rejected(native, bad):
+    import paper_1701_03637_gb300 as sc
+    p = dict(nx=8, ny=8, nz=8)
+    p.update(bad)
+    with pytest.raises(sc.ScError, match="-1"):
+        sc.required_bytes(p)
+
+
+def test_required_bytes_counts_two_lattices(native):
+    import paper_1701_03637_gb300 as sc
+    n = 64 ** 3
+    b32 = sc.required_bytes(dict(nx=64, ny=64, nz=64))
+    b16 = sc.required_bytes(dict(nx=64, ny=64, nz=64, storage="f16"))
+    assert 2 * 2 * 19 * 4 * n <= b32 < 2 * 2 * 19 * 4 * n * 1.05
+    assert 2 * 2 * 19 * 2 * n <= b16 < b32
+    assert len(sc.tile_list()) >= 3

@@ -1,0 +1,240 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs.
+
+Tolerances: one FP32 step of any state is within 1e-6 relative per population
+(denominator max(|f_oracle|, 1e-3 w_i)); densities after 1000 steps are within
+1e-4 absolute. Reduced-precision storage is judged against the oracle applied
+to the same quantised input, within one storage ulp of the offset f - w_i.
+"""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+Q = 19
+
+
+@pytest.fixture(scope="module")
+def sc():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1701_03637_gb300 as mod
+    mod.build()
+    return mod
+
+
+@pytest.fixture(scope="module")
+def W(sc):
+    _, w = sc.lattice_directions()
+    return w
+
+
+def _pair(sc, oracle_mod, params):
+    return sc.Lattice(params), oracle_mod.Lattice(params)
+
+
+def _rel_err(f_gpu, f_orc, w):
+    den = np.maximum(np.abs(f_orc), 1e-3 * w[None, :, None, None, None])
+    return np.max(np.abs(f_gpu - f_orc) / den)
+
+
+GEOMS = {
+    "periodic": dict(),
+    "wall_planar_sink": dict(geometry=1, sink_z0=7, sink_layers=1, wall_z0=0, wall_thickness=2, rho_H=0.03),
+    "seam_sink_2layers": dict(geometry=1, sink_z0=-1, sink_layers=2, rho_H=0.02),
+    "sphere_sink": dict(geometry=2, sphere_cx=10.0, sphere_cy=5.5, sphere_cz=4.0, R_H=4.5, rho_H=0.025),
+    "unequal_tau": dict(tau_r=0.8, tau_b=1.3, G=2.5),
+}
+SHAPES = [(37, 13, 11), (5, 3, 4), (1, 6, 9), (70, 9, 8), (33, 17, 5)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("geom", list(GEOMS))
+def test_one_step_random_state(sc, oracle_mod, W, shape, geom):
+    from paper_1701_03637_gb300.workloads import random_populations
+    nx, ny, nz = shape
+    p = dict(nx=nx, ny=ny, nz=nz, G=3.6)
+    p.update(GEOMS[geom])
+    if p.get("geometry") == 1:
+        p["sink_z0"] = p["sink_z0"] % nz
+        if p.get("wall_thickness", 0) and nz < 8:
+            p["wall_thickness"] = 0
+        p["sink_layers"] = min(p["sink_layers"], nz)
+    g, o = _pair(sc, oracle_mod, p)
+    seed = nx * 10007 + ny * 101 + nz + 1000003 * list(GEOMS).index(geom)
+    f0 = random_populations(nx, ny, nz, seed=seed, rho=(0.55, 0.25))
+    g.write_populations(f0)
+    o.set_populations(f0)
+    # the written state is the oracle's (sink reset applied, solids zeroed) to FP32 rounding
+    assert _rel_err(g.read_populations(), o.populations(), W) < 1e-7
+    g.step(1)
+    o.step(1)
+    assert _rel_err(g.read_populations(), o.populations(), W) < 1e-6
+    dg, do = g.diagnostics(), o.diagnostics()
+    assert dg["step"] == do["step"] == 1
+    assert abs(dg["mass_r"] - do["mass_r"]) <= 1e-6 * abs(do["mass_r"])
+    assert abs(dg["mass_b"] - do["mass_b"]) <= 1e-6 * abs(do["mass_b"])
+    assert abs(dg["flux_last"] - do["flux_last"]) <= 1e-6 * max(1.0, abs(do["mass_r"]))
+    assert dg["droplet_sites"] == do["droplet_sites"]
+
+
+def test_init_shape_matches_oracle(sc, oracle_mod, W):
+    """Device-side SplitMix64 noise and shape equal the oracle's definition."""
+    for params, init in [
+        (dict(nx=12, ny=10, nz=9, geometry=2, sphere_cx=6, sphere_cy=5, sphere_cz=4.5, R_H=4.0),
+         dict(shape=1, cx=6.0, cy=5.0, cz=4.5, radius=3.0, rho_hi=0.7, rho_lo=0.04, noise_amp=1e-2, seed=12345)),
+        (dict(nx=4, ny=4, nz=40, geometry=1, sink_z0=39, wall_thickness=2),
+         dict(shape=0, film_z=10, rho_hi=1.0, rho_lo=0.03, noise_amp=1e-4, seed=0)),
+    ]:
+        g, o = _pair(sc, oracle_mod, params)
+        g.init(init)
+        o.init_shape(init)
+        assert _rel_err(g.read_populations(), o.populations(), W) < 1e-7
+        gr, gb = g.read_fields()
+        orr, ob = o.fields()
+        assert np.max(np.abs(gr - orr)) < 1e-6 and np.max(np.abs(gb - ob)) < 1e-6
+
+
+def test_film_1000_steps(sc, oracle_mod):
+    """4x4x128 film (wall 2, sink plane z=127, rho_H = 0.03, g = 3.6, init 1.0/0.03 with
+    1e-4 noise): densities within 1e-4 absolute after 1000 steps."""
+    from paper_1701_03637_gb300.workloads import film_4x4x128
+    params, init = film_4x4x128()
+    g, o = _pair(sc, oracle_mod, params)
+    g.init(init)
+    o.init_shape(init)
+    g.step(1000)
+    o.step(1000)
+    gr, gb = g.read_fields()
+    orr, ob = o.fields()
+    assert np.max(np.abs(gr - orr)) < 1e-4
+    assert np.max(np.abs(gb - ob)) < 1e-4
+    dg, do = g.diagnostics(), o.diagnostics()
+    assert abs(dg["interface_z"] - do["interface_z"]) < 1e-3
+    assert abs(dg["evaporated_mass"] - do["evaporated_mass"]) < 1e-5 * abs(do["mass_r"])
+    assert abs((dg["mass_r"] + dg["evaporated_mass"]) - (do["mass_r"] + do["evaporated_mass"])) < 1e-5 * do["mass_r"]
+    assert dg["status"] == 0
+
+
+def test_droplet_48_500_steps(sc, oracle_mod):
+    """Droplet with the spherical-exterior sink, 48^3, 500 steps: densities within 1e-4."""
+    from paper_1701_03637_gb300.workloads import droplet
+    params, init = droplet(48, 10.0, 7, spherical_sink=True)
+    g, o = _pair(sc, oracle_mod, params)
+    g.init(init)
+    o.init_shape(init)
+    g.step(500)
+    o.step(500)
+    gr, gb = g.read_fields()
+    orr, ob = o.fields()
+    assert np.max(np.abs(gr - orr)) < 1e-4 and np.max(np.abs(gb - ob)) < 1e-4
+    dg, do = g.diagnostics(), o.diagnostics()
+    assert dg["droplet_sites"] == do["droplet_sites"]
+    assert abs(dg["evaporated_mass"] - do["evaporated_mass"]) < 1e-6 * do["mass_r"]
+
+
+def test_tiles_and_chunks_give_identical_bits(sc):
+    """The per-site arithmetic does not depend on the tile shape, z-chunking or graph replay."""
+    from paper_1701_03637_gb300.workloads import droplet
+    params, init = droplet(40, 9.0, 3, spherical_sink=True)
+    params.update(nx=41, ny=23, nz=19, sphere_cx=20.0, sphere_cy=11.0, sphere_cz=9.0, R_H=9.0)
+    init.update(cx=20.0, cy=11.0, cz=9.0, radius=6.0)
+    ref = None
+    for k, (tile, zc) in enumerate([(1, 0), (2, 3), (3, 1), (4, 19), (1, 5)]):
+        g = sc.Lattice(dict(params, tile=tile, zchunk=zc))
+        g.init(init)
+        if k == 4:
+            for _ in range(30):
+                g.step(1)
+        else:
+            g.step(30)
+        f = g.read_populations()
+        if ref is None:
+            ref = f
+        else:
+            assert np.array_equal(f, ref), (tile, zc)
+
+
+def test_checkpoint_restore(sc, oracle_mod):
+    from paper_1701_03637_gb300.workloads import film_4x4x128
+    params, init = film_4x4x128(rho_hi=0.7, rho_lo=0.04, rho_H=0.01)
+    a = sc.Lattice(params)
+    a.init(init)
+    a.step(300)
+    f = a.read_populations()
+    d = a.diagnostics()
+    b = sc.Lattice(params)
+    b.write_populations(f)
+    b.set_counters(d["step"], d["evaporated_mass"])
+    a.step(300)
+    b.step(300)
+    ra, _ = a.read_fields()
+    rb, _ = b.read_fields()
+    assert np.max(np.abs(ra - rb)) < 1e-6
+    da, db = a.diagnostics(), b.diagnostics()
+    assert da["step"] == db["step"] == 600
+    assert abs(da["evaporated_mass"] - db["evaporated_mass"]) < 1e-6
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+def test_reduced_precision_one_step(sc, oracle_mod, W, storage):
+    """FP16/BF16 offset storage: one step equals the oracle on the same quantised input
+    to within one storage ulp of the offset f - w_i (plus FP32 arithmetic)."""
+    from paper_1701_03637_gb300.workloads import random_populations
+    nx, ny, nz = 37, 13, 11
+    p = dict(nx=nx, ny=ny, nz=nz, G=3.6, storage=storage, **GEOMS["wall_planar_sink"])
+    g = sc.Lattice(p)
+    o = oracle_mod.Lattice(p)
+    g.write_populations(random_populations(nx, ny, nz, seed=9, rho=(0.6, 0.3)))
+    fq = g.read_populations()  # quantised state as the GPU holds it
+    o.set_populations(fq)
+    g.step(1)
+    o.step(1)
+    fg, fo = g.read_populations(), o.populations()
+    off = np.abs(fo - W[None, :, None, None, None])
+    mant = 10 if storage == "f16" else 7
+    ulp = np.exp2(np.floor(np.log2(np.maximum(off, 1e-30))) - mant)
+    ulp = np.maximum(ulp, 2.0 ** -24 if storage == "f16" else 2.0 ** -133)
+    sink = o.site_class() == 1
+    mask = ~np.broadcast_to(sink, fo.shape)  # sink values follow from the arrived totals
+    err = np.abs(fg - fo)
+    assert np.all(err[mask] <= 1.01 * ulp[mask] + 1e-7 * np.abs(fo[mask]))
+
+
+def test_full_size_sampled_windows(sc, oracle_mod):
+    """128^3 droplet in the benchmark's launch configuration: one GPU step, checked at
+    sampled sites against the oracle run on a 7^3 window around each site (the step
+    reaches two sites, so the window's own periodic seam cannot reach the centre)."""
+    from paper_1701_03637_gb300.workloads import droplet
+    n = 128
+    params, init = droplet(n, 24.0, 1)
+    g = sc.Lattice(params)
+    g.init(init)
+    r0, b0 = g.read_fields()
+    g.step(1)
+    r1, b1 = g.read_fields()
+    # total mass is conserved exactly by the sink's complement rule
+    assert abs((r1.sum(dtype=np.float64) + b1.sum(dtype=np.float64)) /
+               (r0.sum(dtype=np.float64) + b0.sum(dtype=np.float64)) - 1) < 1e-6
+    rng = np.random.default_rng(5)
+    pts = [(64, 64, 64), (64, 64, 64 + 24), (88, 64, 64), (10, 100, 126), (3, 5, 127), (7, 9, 0), (0, 0, 1),
+           (127, 127, 126)] + [tuple(int(v) for v in rng.integers(0, n, 3)) for _ in range(8)]
+    for (X, Y, Z) in pts:
+        xs = np.arange(X - 3, X + 4) % n
+        ys = np.arange(Y - 3, Y + 4) % n
+        zs = np.arange(Z - 3, Z + 4) % n
+        wr = r0[np.ix_(zs, ys, xs)].astype(np.float64)
+        wb = b0[np.ix_(zs, ys, xs)].astype(np.float64)
+        wp = dict(nx=7, ny=7, nz=7, G=params["G"], rho_H=params["rho_H"])
+        sink_planes = [k for k, z in enumerate(zs) if z in (n - 1, 0)]
+        if sink_planes:
+            wp.update(geometry=1, sink_z0=sink_planes[0], sink_layers=len(sink_planes))
+        o = oracle_mod.Lattice(wp)
+        o.init_fields(wr, wb)
+        o.step(1)
+        orr, ob = o.fields()
+        assert abs(r1[Z, Y, X] - orr[3, 3, 3]) < 1e-6 * max(1.0, orr[3, 3, 3]), (X, Y, Z)
+        assert abs(b1[Z, Y, X] - ob[3, 3, 3]) < 1e-6 * max(1.0, ob[3, 3, 3]), (X, Y, Z)
