@@ -37,8 +37,14 @@ __host__ __device__ constexpr int dir_z(int i) {
        : (i == 6 || i == 12 || i == 13 || i == 16 || i == 17) ? -1 : 0;
 }
 __host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
-// Lattice weights (Sec. II A): 1/3 rest, 1/18 axis, 1/36 diagonal.
-__host__ __device__ constexpr float wgt(int i) { return i == 0 ? 1.0f / 3.0f : (i <= 6 ? 1.0f / 18.0f : 1.0f / 36.0f); }
+// Lattice weights (Sec. II A): 1/3 rest, 1/18 axis, 1/36 diagonal. In FP32 they are
+// chosen within two ulps of those values so that w0 + 6 w1 + 12 w2 == 1 exactly:
+// with the nearest floats the sum is 1 + 2^-26 and every collision would create
+// that fraction of its mass (a steady drift of the conserved totals).
+constexpr float kW1 = 14913080.0f * 0x1p-28f;  // 1/18 - 1 ulp
+constexpr float kW2 = 7456540.0f * 0x1p-28f;   // kW1 / 2 exactly
+constexpr float kW0 = 11184812.0f * 0x1p-25f;  // 1 - 12 kW1 exactly
+__host__ __device__ constexpr float wgt(int i) { return i == 0 ? kW0 : (i <= 6 ? kW1 : kW2); }
 __host__ __device__ constexpr double wgt_d(int i) { return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0); }
 
 // Everything a launch needs to know about one lattice.
@@ -47,7 +53,7 @@ struct LatDev {
   long long np;            // elements between consecutive direction arrays
   float omega[2], tau[2];  // 1/tau and tau per component
   float G, rhoH;           // g of Eq. (3); imposed rho^r at sinks
-  double rhoH_d;
+  double rhoH_mass;         // exact sum of the reset r populations fl(w_i rho_H)
   int geometry, sink_z0, sink_layers;
   double scx, scy, scz, RH2;
   int wall_z0, wall_z1;    // solid slab [wall_z0, wall_z1)
@@ -179,6 +185,19 @@ __device__ __forceinline__ void sink_densities(const LatDev& L, float& rr, float
   rb = rbn;
 }
 
+// Reset value of direction i for density rho (f^eq at rest), an exact float product.
+__device__ __forceinline__ float rest_pop(int i, float rho) { return __fmul_rn(wgt(i), rho); }
+
+// Evaporated mass of one sink site: sum_i (f_i^r - w_i rho_H) over the arrived r
+// populations, without contraction, so that where only reset values arrived (inside
+// the sink region) every term is exactly zero and no rounding bias is booked.
+__device__ __forceinline__ float sink_excess(const LatDev& L, const float (&fr)[Q]) {
+  float e = 0.0f;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) e = __fadd_rn(e, __fsub_rn(fr[i], rest_pop(i, L.rhoH)));
+  return e;
+}
+
 __device__ __forceinline__ float psi_of(float rho) { return 1.0f - expf(-rho); }  // Eq. (4), rho0 = 1
 
 // Shifted-velocity BGK collision of one fluid site, storing f* (Eqs. (1)-(3)).
@@ -212,16 +231,28 @@ __device__ __forceinline__ void collide_store(const LatDev& L, typename S::T* __
   const float usr = ur[0] * ur[0] + ur[1] * ur[1] + ur[2] * ur[2];
   const float usb = ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2];
   const long long cstride = (long long)Q * L.np;
-  Unroll<0, Q>::run([&](auto ic) {
-    constexpr int I = decltype(ic)::value;
+  // f^eq_i = w_i rho (1 + 3 c.u + 4.5 (c.u)^2 - 1.5 u.u); opposite directions share
+  // the even part and differ in the sign of the odd part.
+  {
+    const float feqr = kW0 * rr * (1.0f - 1.5f * usr);
+    const float feqb = kW0 * rb * (1.0f - 1.5f * usb);
+    S::st(dst + s, fr[0] + omr * (feqr - fr[0]), kW0);
+    S::st(dst + s + cstride, fb[0] + omb * (feqb - fb[0]), kW0);
+  }
+  Unroll<0, 9>::run([&](auto kc) {
+    constexpr int I = 1 + 2 * decltype(kc)::value, J = I + 1;
     constexpr float w = wgt(I);
     const float cur = (float)dir_x(I) * ur[0] + (float)dir_y(I) * ur[1] + (float)dir_z(I) * ur[2];
     const float cub = (float)dir_x(I) * ub[0] + (float)dir_y(I) * ub[1] + (float)dir_z(I) * ub[2];
-    const float feqr = w * rr * (1.0f + 3.0f * cur + 4.5f * cur * cur - 1.5f * usr);
-    const float feqb = w * rb * (1.0f + 3.0f * cub + 4.5f * cub * cub - 1.5f * usb);
-    typename S::T* p = dst + (long long)I * L.np + s;
-    S::st(p, fr[I] + omr * (feqr - fr[I]), w);
-    S::st(p + cstride, fb[I] + omb * (feqb - fb[I]), w);
+    const float wrr = w * rr, wrb = w * rb;
+    const float evr = wrr * (1.0f + 4.5f * cur * cur - 1.5f * usr), odr = wrr * (3.0f * cur);
+    const float evb = wrb * (1.0f + 4.5f * cub * cub - 1.5f * usb), odb = wrb * (3.0f * cub);
+    typename S::T* pi = dst + (long long)I * L.np + s;
+    typename S::T* pj = dst + (long long)J * L.np + s;
+    S::st(pi, fr[I] + omr * ((evr + odr) - fr[I]), w);
+    S::st(pj, fr[J] + omr * ((evr - odr) - fr[J]), w);
+    S::st(pi + cstride, fb[I] + omb * ((evb + odb) - fb[I]), w);
+    S::st(pj + cstride, fb[J] + omb * ((evb - odb) - fb[J]), w);
   });
 }
 
@@ -264,9 +295,11 @@ struct Tile {
   bool active, has_halo;
   double evap;
 
-  __device__ __forceinline__ Tile(const LatDev& L_, Smem& sm_, const typename S::T* s_, typename S::T* d_, int bx,
-                                  int by)
-      : L(L_), sm(sm_), src(s_), dst(d_), evap(0.0) {
+  __device__ __forceinline__ Tile(const LatDev& L_, Smem& sm_, const typename S::T* s_, typename S::T* d_)
+      : L(L_), sm(sm_), src(s_), dst(d_), evap(0.0) {}
+
+  // Bind the CTA to tile column (bx, by).
+  __device__ __forceinline__ void setup(int bx, int by) {
     const int tid = threadIdx.x;
     tx = tid % TX;
     ty = tid / TX;
@@ -298,7 +331,7 @@ struct Tile {
       rr = sum19(fr);
       rb = sum19(fb);
       if (cls == SINK) {
-        if (active && own) evap += (double)rr - L.rhoH_d;
+        if (active && own) evap += (double)sink_excess(L, fr);
         sink_densities(L, rr, rb);
       }
       pr = psi_of(rr);
@@ -330,7 +363,7 @@ struct Tile {
       // Sinks are neither forced nor collided: they stream f^eq(rho_H, 0) and
       // f^eq(rho^r + rho^b - rho_H, 0) as they are.
 #pragma unroll
-      for (int i = 0; i < Q; ++i) { fr[i] = wgt(i) * rr; fb[i] = wgt(i) * rb; }
+      for (int i = 0; i < Q; ++i) { fr[i] = rest_pop(i, rr); fb[i] = rest_pop(i, rb); }
       store_plain<S>(L, dst, s, fr, fb);
       return;
     }
@@ -353,21 +386,28 @@ struct Tile {
     collide_store<S>(L, dst, s, fr, fb, rr, rb, psr, psb, ar, ab);
   }
 
-  // March planes [zb, ze); returns this thread's evaporated-mass share.
-  __device__ __forceinline__ void run(int zb, int ze) {
+  // March planes [zb, ze) upward (down = false) or downward. Each plane is staged
+  // one plane ahead of its collision; the halo plane on the far side is staged
+  // for Psi only.
+  __device__ __forceinline__ void run(int zb, int ze, bool down) {
     float ar_[Q], ab_[Q], br_[Q], bb_[Q];
     float arr, arb, brr, brb;
     int acl, bcl;
-    stage(zb - 1, false, ar_, ab_, arr, arb, acl);
-    stage(zb, true, ar_, ab_, arr, arb, acl);
-    for (int z = zb; z < ze; z += 2) {
-      stage(z + 1, z + 1 < ze, br_, bb_, brr, brb, bcl);
+    const int d = down ? -1 : 1;
+    const int first = down ? ze - 1 : zb;
+    const int n = ze - zb;
+    auto own = [&](int p) { return p >= zb && p < ze; };
+    stage(first - d, false, ar_, ab_, arr, arb, acl);
+    stage(first, true, ar_, ab_, arr, arb, acl);
+    for (int k = 0; k < n; k += 2) {
+      const int z = first + d * k;
+      stage(z + d, own(z + d), br_, bb_, brr, brb, bcl);
       __syncthreads();
       finish(z, ar_, ab_, arr, arb, acl);
-      if (z + 1 >= ze) break;
-      stage(z + 2, z + 2 < ze, ar_, ab_, arr, arb, acl);
+      if (k + 1 >= n) break;
+      stage(z + 2 * d, own(z + 2 * d), ar_, ab_, arr, arb, acl);
       __syncthreads();
-      finish(z + 1, br_, bb_, brr, brb, bcl);
+      finish(z + d, br_, bb_, brr, brb, bcl);
     }
   }
 

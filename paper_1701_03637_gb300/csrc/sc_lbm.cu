@@ -43,22 +43,32 @@ size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
 // ------------------------------------------------------------------ kernels
 
+// Persistent fused step. The lattice is cut into tile columns of TX x TY sites
+// and z into nch chunks; item i = (chunk i / cols, column i % cols). CTA b takes
+// items b, b + G, b + 2G, ... so in every round the G resident CTAs work on
+// neighbouring columns of the same chunk in lock-step, and a column's halo and
+// shifted-pull sectors are read from DRAM once and then from L2 by its
+// neighbours. Chunks alternate their marching direction.
 template <int TX, int TY, class S>
 __global__ void __launch_bounds__(TX * TY, 2)
     k_step(const LatDev L, const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
-           double* __restrict__ evap_cum, int zchunk) {
+           double* __restrict__ evap_cum, int cols_x, int cols, int nch) {
   using TileT = Tile<TX, TY, S>;
   __shared__ typename TileT::Smem sm;
-  TileT t(L, sm, src, dst, blockIdx.x, blockIdx.y);
-  const int zb = blockIdx.z * zchunk;
-  const int ze = min(zb + zchunk, L.nz);
-  t.run(zb, ze);
+  TileT t(L, sm, src, dst);
+  const long long items = (long long)cols * nch;
+  bool first = true;
+  for (long long it = blockIdx.x; it < items; it += gridDim.x) {
+    const int k = (int)(it / cols), c = (int)(it - (long long)k * cols);
+    const int zb = (int)((long long)k * L.nz / nch), ze = (int)((long long)(k + 1) * L.nz / nch);
+    if (!first) __syncthreads();  // the previous item's last reads of the ring
+    t.setup(c % cols_x, c / cols_x);
+    t.run(zb, ze, (k & 1) != 0);
+    first = false;
+  }
   if (L.geometry != 0) {
     const double e = t.block_evap();
-    if (threadIdx.x == 0) {
-      const long long slot = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-      evap_cum[slot] += e;
-    }
+    if (threadIdx.x == 0) evap_cum[blockIdx.x] += e;
   }
 }
 
@@ -84,7 +94,7 @@ __global__ void k_canonical(const LatDev L, const typename S::T* __restrict__ sr
       if (cls == SINK) {
         sink_densities(L, rr, rb);
 #pragma unroll
-        for (int i = 0; i < Q; ++i) { fr[i] = wgt(i) * rr; fb[i] = wgt(i) * rb; }
+        for (int i = 0; i < Q; ++i) { fr[i] = rest_pop(i, rr); fb[i] = rest_pop(i, rb); }
       }
     }
     const long long o = s - s0;
@@ -119,15 +129,18 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag(const LatDev L, const typ
       const int x = q % L.nx, y = q / L.nx;
       const int cls = site_class(L, x, y, z);
       const PullIdx P(L, x, y, z);
-      float rr, rb;
-      pull_sums<S>(L, src, P, rr, rb);
+      float fr[Q], fb[Q];
+      pull_full<S>(L, src, P, fr, fb);
+      float rr = sum19(fr), rb = sum19(fb);
+      double mr = rr;
       if (cls == SINK) {
-        acc[3] += (double)rr - L.rhoH_d;
+        acc[3] += (double)sink_excess(L, fr);
         sink_densities(L, rr, rb);
+        mr = L.rhoH_mass;
         if (rb < 0.0f) acc[6] = 1.0;
       }
       if (!isfinite(rr) || !isfinite(rb)) acc[5] = 1.0;
-      acc[0] += rr;
+      acc[0] += mr;
       acc[1] += rb;
       acc[2] += (double)rr - (double)rb;
       acc[4] += rr > rb ? 1.0 : 0.0;
@@ -215,7 +228,7 @@ __global__ void k_load(const LatDev L, typename S::T* __restrict__ dst, long lon
       float rr = sum19(fr), rb = sum19(fb);
       sink_densities(L, rr, rb);
 #pragma unroll
-      for (int i = 0; i < Q; ++i) { fr[i] = wgt(i) * rr; fb[i] = wgt(i) * rb; }
+      for (int i = 0; i < Q; ++i) { fr[i] = rest_pop(i, rr); fb[i] = rest_pop(i, rb); }
     }
     // inverse of the pull: f_i(x) is read from x - e_i, or from (x, opp(i)) when
     // x - e_i is solid.
@@ -234,34 +247,46 @@ __global__ void k_load(const LatDev L, typename S::T* __restrict__ dst, long lon
 
 // ------------------------------------------------------------------ launch tables
 
-using StepFn = void (*)(const LatDev, const void*, void*, double*, int);
-
 template <int TX, int TY, class S>
-cudaError_t launch_step(const LatDev& L, const void* src, void* dst, double* evap, int zchunk, dim3 grid,
-                        cudaStream_t st) {
-  k_step<TX, TY, S><<<grid, TX * TY, 0, st>>>(L, (const typename S::T*)src, (typename S::T*)dst, evap, zchunk);
+cudaError_t launch_step(const LatDev& L, const void* src, void* dst, double* evap, int cols_x, int cols, int nch,
+                        int G, cudaStream_t st) {
+  k_step<TX, TY, S><<<G, TX * TY, 0, st>>>(L, (const typename S::T*)src, (typename S::T*)dst, evap, cols_x, cols,
+                                            nch);
   return cudaGetLastError();
 }
 
-using LaunchFn = cudaError_t (*)(const LatDev&, const void*, void*, double*, int, dim3, cudaStream_t);
+template <int TX, int TY, class S>
+int occupancy_step() {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step<TX, TY, S>, TX * TY, 0) != cudaSuccess) return 1;
+  return std::max(nb, 1);
+}
+
+using LaunchFn = cudaError_t (*)(const LatDev&, const void*, void*, double*, int, int, int, int, cudaStream_t);
+struct StepOps {
+  LaunchFn launch;
+  int (*occupancy)();
+};
 
 template <class S>
-LaunchFn pick_step(int tile) {
+StepOps pick_step(int tile) {
   switch (tile) {
-    case 0: return &launch_step<32, 8, S>;
-    case 1: return &launch_step<32, 4, S>;
-    case 2: return &launch_step<16, 8, S>;
-    default: return &launch_step<8, 4, S>;
+    case 0: return {&launch_step<32, 8, S>, &occupancy_step<32, 8, S>};
+    case 1: return {&launch_step<32, 4, S>, &occupancy_step<32, 4, S>};
+    case 2: return {&launch_step<16, 8, S>, &occupancy_step<16, 8, S>};
+    default: return {&launch_step<8, 4, S>, &occupancy_step<8, 4, S>};
   }
 }
 
-LaunchFn step_fn(int storage, int tile) {
+StepOps step_ops(int storage, int tile) {
   switch (storage) {
     case SC_STORAGE_F16: return pick_step<StF16>(tile);
     case SC_STORAGE_BF16: return pick_step<StBF16>(tile);
     default: return pick_step<StF32>(tile);
   }
 }
+
+constexpr long long kMaxCtas = 4096;  // evaporated-mass slots, one per CTA of the persistent step
 
 size_t elem_size(int storage) { return storage == SC_STORAGE_F32 ? 4 : 2; }
 
@@ -285,10 +310,8 @@ int validate(const sc_params* p) {
 }
 
 struct Layout {
-  int tile, tx, ty, zchunk;
-  long long np, nsites;
-  dim3 grid;
-  long long nctas;
+  int tile, tx, ty, cols_x, cols;
+  long long np, nsites, units, nslots;
   int diag_nsplit;
   size_t off_pop[2], off_stage, off_evap, off_diag, total;
 };
@@ -306,18 +329,10 @@ Layout make_layout(const sc_params* p) {
   l.ty = kTileY[l.tile];
   l.nsites = (long long)p->nx * p->ny * p->nz;
   l.np = (l.nsites + 127) / 128 * 128;
-  const long long cols = (long long)((p->nx + l.tx - 1) / l.tx) * ((p->ny + l.ty - 1) / l.ty);
-  int zc = p->zchunk;
-  if (zc <= 0) {
-    const long long target = 4LL * 152;  // about two waves at two CTAs per SM
-    long long nch = (target + cols - 1) / cols;
-    nch = std::max(1LL, std::min<long long>(nch, p->nz));
-    zc = (int)((p->nz + nch - 1) / nch);
-  }
-  zc = std::min(zc, p->nz);
-  l.zchunk = zc;
-  l.grid = dim3((p->nx + l.tx - 1) / l.tx, (p->ny + l.ty - 1) / l.ty, (p->nz + zc - 1) / zc);
-  l.nctas = (long long)l.grid.x * l.grid.y * l.grid.z;
+  l.cols_x = (p->nx + l.tx - 1) / l.tx;
+  l.cols = l.cols_x * ((p->ny + l.ty - 1) / l.ty);
+  l.units = (long long)l.cols * p->nz;
+  l.nslots = std::min(l.units, kMaxCtas);
   const long long per_plane = (long long)p->nx * p->ny;
   l.diag_nsplit = (int)std::max(1LL, std::min<long long>((4LL * 152 + p->nz - 1) / p->nz, (per_plane + 1023) / 1024));
   const size_t pop = align256((size_t)2 * Q * l.np * elem_size(p->storage));
@@ -325,7 +340,7 @@ Layout make_layout(const sc_params* p) {
   l.off_pop[0] = off; off += pop;
   l.off_pop[1] = off; off += pop;
   l.off_stage = off; off += align256((size_t)2 * l.np * sizeof(float));
-  l.off_evap = off; off += align256((size_t)l.nctas * sizeof(double));
+  l.off_evap = off; off += align256((size_t)l.nslots * sizeof(double));
   l.off_diag = off; off += align256((size_t)p->nz * l.diag_nsplit * kDiagFields * sizeof(double));
   l.total = off;
   return l;
@@ -339,7 +354,8 @@ LatDev make_dev(const sc_params* p, const Layout& l) {
   L.omega[0] = (float)(1.0 / p->tau_r); L.omega[1] = (float)(1.0 / p->tau_b);
   L.G = (float)p->G;
   L.rhoH = (float)p->rho_H;
-  L.rhoH_d = (double)(float)p->rho_H;
+  L.rhoH_mass = 0.0;
+  for (int i = 0; i < Q; ++i) L.rhoH_mass += (double)(wgt(i) * (float)p->rho_H);
   L.geometry = p->geometry;
   L.sink_z0 = p->sink_z0; L.sink_layers = p->sink_layers;
   L.scx = p->sphere_cx; L.scy = p->sphere_cy; L.scz = p->sphere_cz; L.RH2 = p->R_H * p->R_H;
@@ -362,6 +378,8 @@ struct sc_lbm {
   double evap_offset;  // evaporated mass restored by sc_lbm_set_counters
   double* h_diag;      // pinned
   double* h_evap;      // pinned
+  int grid;  // CTAs of the persistent step
+  int nch;   // z chunks per tile column
   cudaGraphExec_t graph;
   int graph_len;
   int graph_cur;
@@ -375,8 +393,9 @@ namespace {
 
 int launch_one(sc_lbm* h, cudaStream_t st) {
   const int src = h->cur, dst = 1 - h->cur;
-  cudaError_t e = step_fn(h->p.storage, h->lay.tile)(h->L, h->pop(src), h->pop(dst), h->evap(), h->lay.zchunk,
-                                                      h->lay.grid, st);
+  cudaError_t e = step_ops(h->p.storage, h->lay.tile)
+                      .launch(h->L, h->pop(src), h->pop(dst), h->evap(), h->lay.cols_x, h->lay.cols, h->nch, h->grid,
+                              st);
   if (e != cudaSuccess) return fail(SC_ECUDA, "step launch failed: %s", cudaGetErrorString(e));
   h->cur = dst;
   return SC_OK;
@@ -433,7 +452,7 @@ int launch_diag(sc_lbm* h) {
 }
 
 int reset_counters(sc_lbm* h) {
-  CK(cudaMemsetAsync(h->evap(), 0, sizeof(double) * h->lay.nctas, h->stream));
+  CK(cudaMemsetAsync(h->evap(), 0, sizeof(double) * h->lay.nslots, h->stream));
   h->step = 0;
   h->evap_offset = 0.0;
   return SC_OK;
@@ -486,8 +505,36 @@ static int create_common(const sc_params* p, void* stream, void* buf, size_t byt
   h->graph = nullptr;
   h->graph_len = 0;
   h->graph_cur = 0;
-  cudaError_t e = cudaMallocHost((void**)&h->h_diag, sizeof(double) * p->nz * h->lay.diag_nsplit * kDiagFields);
-  if (e == cudaSuccess) e = cudaMallocHost((void**)&h->h_evap, sizeof(double) * h->lay.nctas);
+  // persistent grid: every resident CTA slot, or one CTA per zchunk planes of work
+  int dev = 0, sms = 1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) {
+    if (owns) cudaFree(buf);
+    delete h;
+    return fail(SC_ECUDA, "device query failed: %s", cudaGetErrorString(e));
+  }
+  // Persistent grid of every resident CTA slot. The z chunk count trades rounds
+  // (ceil(items / G)) against the two extra planes each item stages; a caller
+  // zchunk > 0 fixes the chunk length instead.
+  const long long slots = std::min<long long>((long long)sms * step_ops(p->storage, h->lay.tile).occupancy(),
+                                              h->lay.nslots);
+  const long long cols = h->lay.cols;
+  long long best_nch = 1;
+  if (p->zchunk > 0) {
+    best_nch = (p->nz + p->zchunk - 1) / p->zchunk;
+  } else {
+    double best = 1e300;
+    for (long long nch = 1; nch <= p->nz; ++nch) {
+      const long long rounds = (cols * nch + slots - 1) / slots;
+      const double cost = (double)rounds * ((double)((p->nz + nch - 1) / nch) + 2.0);
+      if (cost < best * (1.0 - 1e-9)) { best = cost; best_nch = nch; }
+    }
+  }
+  h->nch = (int)best_nch;
+  h->grid = (int)std::max(1LL, std::min<long long>(slots, cols * best_nch));
+  e = cudaMallocHost((void**)&h->h_diag, sizeof(double) * p->nz * h->lay.diag_nsplit * kDiagFields);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&h->h_evap, sizeof(double) * h->lay.nslots);
   if (e != cudaSuccess) {
     if (h->h_diag) cudaFreeHost(h->h_diag);
     if (owns) cudaFree(buf);
@@ -680,7 +727,7 @@ int sc_lbm_write_populations(sc_lbm* h, const double* f) {
 
 int sc_lbm_set_counters(sc_lbm* h, int64_t step, double evaporated) {
   if (!h) return fail(SC_EINVAL, "NULL handle");
-  CK(cudaMemsetAsync(h->evap(), 0, sizeof(double) * h->lay.nctas, h->stream));
+  CK(cudaMemsetAsync(h->evap(), 0, sizeof(double) * h->lay.nslots, h->stream));
   h->step = step;
   h->evap_offset = evaporated;
   return SC_OK;
@@ -696,7 +743,7 @@ static int run_diag(sc_lbm* h) {
   if (rc) return rc;
   const size_t nd = (size_t)h->p.nz * h->lay.diag_nsplit * kDiagFields;
   CK(cudaMemcpyAsync(h->h_diag, h->diag(), sizeof(double) * nd, cudaMemcpyDeviceToHost, h->stream));
-  CK(cudaMemcpyAsync(h->h_evap, h->evap(), sizeof(double) * h->lay.nctas, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(h->h_evap, h->evap(), sizeof(double) * h->lay.nslots, cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   return SC_OK;
 }
@@ -738,7 +785,7 @@ int sc_lbm_diagnostics(sc_lbm* h, sc_diag* d) {
     phi[z] = (h->L.wall_z0 <= z && z < h->L.wall_z1) ? NAN : pz / (double)h->L.nxny;
   }
   double cum = 0.0;
-  for (long long k = 0; k < h->lay.nctas; ++k) cum += h->h_evap[k];
+  for (long long k = 0; k < h->lay.nslots; ++k) cum += h->h_evap[k];
   d->step = h->step;
   d->evaporated_mass = h->evap_offset + cum + pending;
   d->flux_last = pending;
@@ -762,14 +809,14 @@ int sc_lbm_launch_info(sc_lbm* h, int32_t* tx, int32_t* ty, int32_t* zchunk, int
   if (!h) return fail(SC_EINVAL, "NULL handle");
   if (tx) *tx = h->lay.tx;
   if (ty) *ty = h->lay.ty;
-  if (zchunk) *zchunk = h->lay.zchunk;
-  if (ctas) *ctas = h->lay.nctas;
+  if (zchunk) *zchunk = (int32_t)((h->p.nz + h->nch - 1) / h->nch);
+  if (ctas) *ctas = h->grid;
   return SC_OK;
 }
 
 int sc_lbm_diag_bytes(sc_lbm* h, size_t* bytes) {
   if (!h || !bytes) return fail(SC_EINVAL, "NULL argument");
-  *bytes = sizeof(double) * ((size_t)h->p.nz * h->lay.diag_nsplit * kDiagFields + (size_t)h->lay.nctas);
+  *bytes = sizeof(double) * ((size_t)h->p.nz * h->lay.diag_nsplit * kDiagFields + (size_t)h->lay.nslots);
   return SC_OK;
 }
 
