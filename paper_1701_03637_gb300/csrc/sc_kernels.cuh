@@ -1,13 +1,17 @@
 // Device code for the two-component Shan-Chen D3Q19 evaporation step
-// (arXiv:1701.03637, Sec. II). Shared by the single-lattice and batched launches.
+// (arXiv:1701.03637, Sec. II) shared by all launches of the library.
 //
 // State between launches ("pre-stream" form): the buffer holds post-collision
 // populations f*(t-1). One launch pulls them (streaming with halfway
 // bounce-back), applies the evaporation sink to the arrived populations, forms
-// densities and Psi, the Eq. (3) force from a shared-memory Psi tile with a
-// one-site halo, and collides (Eqs. (1), (2) with the tau F / rho velocity
-// shift), writing f*(t) to the other buffer. The canonical (post-stream,
-// post-sink) populations of step t are therefore pull + sink of the buffer.
+// densities and Psi, the Eq. (3) force, and collides (Eqs. (1), (2) with the
+// tau F / rho velocity shift), writing f*(t) to the other buffer. The canonical
+// (post-stream, post-sink) populations of step t are pull + sink of the buffer.
+//
+// Memory layout: 2 x 19 arrays (component-major, then direction) of np elements;
+// site s = x + nx (y + ny z) with x fastest, rows contiguous without padding so
+// that neighbouring tiles share every fetched sector through L2. Periodic wrap
+// is index arithmetic.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -50,10 +54,10 @@ __host__ __device__ constexpr double wgt_d(int i) { return i == 0 ? 1.0 / 3.0 : 
 // Everything a launch needs to know about one lattice.
 struct LatDev {
   int nx, ny, nz, nxny;
-  long long np;            // elements between consecutive direction arrays
+  long long np;            // elements between consecutive (component, direction) arrays
   float omega[2], tau[2];  // 1/tau and tau per component
   float G, rhoH;           // g of Eq. (3); imposed rho^r at sinks
-  double rhoH_mass;         // exact sum of the reset r populations fl(w_i rho_H)
+  double rhoH_mass;        // exact sum of the reset r populations fl(w_i rho_H)
   int geometry, sink_z0, sink_layers;
   double scx, scy, scz, RH2;
   int wall_z0, wall_z1;    // solid slab [wall_z0, wall_z1)
@@ -63,21 +67,24 @@ struct LatDev {
 struct StF32 {
   using T = float;
   static __device__ __forceinline__ float ld(const T* p, float) { return __ldg(p); }
+  static __device__ __forceinline__ float cv(T v, float) { return v; }
   static __device__ __forceinline__ void st(T* p, float v, float) { *p = v; }
 };
 // FP16 / BF16 offsets h = f - w_i * rho0 (rho0 = 1), round to nearest even.
 struct StF16 {
   using T = __half;
   static __device__ __forceinline__ float ld(const T* p, float w) { return w + __half2float(__ldg(p)); }
+  static __device__ __forceinline__ float cv(T v, float w) { return w + __half2float(v); }
   static __device__ __forceinline__ void st(T* p, float v, float w) { *p = __float2half_rn(v - w); }
 };
 struct StBF16 {
   using T = __nv_bfloat16;
   static __device__ __forceinline__ float ld(const T* p, float w) { return w + __bfloat162float(__ldg(p)); }
+  static __device__ __forceinline__ float cv(T v, float w) { return w + __bfloat162float(v); }
   static __device__ __forceinline__ void st(T* p, float v, float w) { *p = __float2bfloat16_rn(v - w); }
 };
 
-__device__ __forceinline__ int wrapi(int v, int n) {
+__host__ __device__ __forceinline__ int wrapi(int v, int n) {
   v %= n;
   return v < 0 ? v + n : v;
 }
@@ -85,8 +92,8 @@ __device__ __forceinline__ int wrapi(int v, int n) {
 __device__ __forceinline__ bool solid_z(const LatDev& L, int z) { return z >= L.wall_z0 && z < L.wall_z1; }
 
 // Site class from coordinates (no storage): solid slab, planar or spherical sink.
-// The squared distance is formed without FMA contraction so it rounds the same
-// way as a plain host evaluation.
+// The squared distance is formed without FMA contraction so it rounds like a
+// plain host evaluation.
 __device__ __forceinline__ int site_class(const LatDev& L, int x, int y, int z) {
   if (solid_z(L, z)) return SOLID;
   if (L.geometry == 1) return wrapi(z - L.sink_z0, L.nz) < L.sink_layers ? SINK : FLUID;
@@ -98,9 +105,23 @@ __device__ __forceinline__ int site_class(const LatDev& L, int x, int y, int z) 
   return FLUID;
 }
 
+template <int I, int N>
+struct Unroll {
+  template <class F>
+  static __device__ __forceinline__ void run(F&& f) {
+    f(std::integral_constant<int, I>());
+    Unroll<I + 1, N>::run(f);
+  }
+};
+template <int N>
+struct Unroll<N, N> {
+  template <class F>
+  static __device__ __forceinline__ void run(F&&) {}
+};
+
 // Source offsets of the pull for site (x, y, z): the population arriving in
-// direction i comes from x - e_i; from a solid site it is the site's own
-// opposite population (halfway bounce-back).
+// direction i comes from x - e_i (periodic); from a solid site it is the site's
+// own opposite population (halfway bounce-back).
 struct PullIdx {
   int xs[3], ys[3], zs[3];  // indexed by 1 + e (source = x - e)
   bool sol_m, sol_p;        // source plane z - 1 / z + 1 is solid
@@ -123,20 +144,6 @@ struct PullIdx {
     idx = sol ? s : xs[1 + ex] + ys[1 + ey] + zs[1 + ez];
     d = sol ? opp(I) : I;
   }
-};
-
-template <int I, int N>
-struct Unroll {
-  template <class F>
-  static __device__ __forceinline__ void run(F&& f) {
-    f(std::integral_constant<int, I>());
-    Unroll<I + 1, N>::run(f);
-  }
-};
-template <int N>
-struct Unroll<N, N> {
-  template <class F>
-  static __device__ __forceinline__ void run(F&&) {}
 };
 
 template <class S>
@@ -200,65 +207,9 @@ __device__ __forceinline__ float sink_excess(const LatDev& L, const float (&fr)[
 
 __device__ __forceinline__ float psi_of(float rho) { return 1.0f - expf(-rho); }  // Eq. (4), rho0 = 1
 
-// Shifted-velocity BGK collision of one fluid site, storing f* (Eqs. (1)-(3)).
-// ar/ab: sum_i w_i Psi^{r|b}(x + e_i) e_i.
 template <class S>
-__device__ __forceinline__ void collide_store(const LatDev& L, typename S::T* __restrict__ dst, int s,
-                                              const float (&fr)[Q], const float (&fb)[Q], float rr, float rb,
-                                              float psr, float psb, const float (&ar)[3], const float (&ab)[3]) {
-  const float omr = L.omega[0], omb = L.omega[1];
-  float mr[3] = {0.f, 0.f, 0.f}, mb[3] = {0.f, 0.f, 0.f};
-  Unroll<1, Q>::run([&](auto ic) {
-    constexpr int I = decltype(ic)::value;
-    if (dir_x(I) > 0) { mr[0] += fr[I]; mb[0] += fb[I]; }
-    if (dir_x(I) < 0) { mr[0] -= fr[I]; mb[0] -= fb[I]; }
-    if (dir_y(I) > 0) { mr[1] += fr[I]; mb[1] += fb[I]; }
-    if (dir_y(I) < 0) { mr[1] -= fr[I]; mb[1] -= fb[I]; }
-    if (dir_z(I) > 0) { mr[2] += fr[I]; mb[2] += fb[I]; }
-    if (dir_z(I) < 0) { mr[2] -= fr[I]; mb[2] -= fb[I]; }
-  });
-  const float den = rr * omr + rb * omb;
-  const float inv = den > 0.0f ? 1.0f / den : 0.0f;
-  float ur[3], ub[3];
-  const float sr = rr > 0.0f ? L.tau[0] / rr : 0.0f;
-  const float sb = rb > 0.0f ? L.tau[1] / rb : 0.0f;
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    const float up = (mr[d] * omr + mb[d] * omb) * inv;  // common velocity u'
-    ur[d] = up + sr * (-L.G * psr * ab[d]);               // u' + tau F^r / rho^r
-    ub[d] = up + sb * (-L.G * psb * ar[d]);               // u' + tau F^b / rho^b
-  }
-  const float usr = ur[0] * ur[0] + ur[1] * ur[1] + ur[2] * ur[2];
-  const float usb = ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2];
-  const long long cstride = (long long)Q * L.np;
-  // f^eq_i = w_i rho (1 + 3 c.u + 4.5 (c.u)^2 - 1.5 u.u); opposite directions share
-  // the even part and differ in the sign of the odd part.
-  {
-    const float feqr = kW0 * rr * (1.0f - 1.5f * usr);
-    const float feqb = kW0 * rb * (1.0f - 1.5f * usb);
-    S::st(dst + s, fr[0] + omr * (feqr - fr[0]), kW0);
-    S::st(dst + s + cstride, fb[0] + omb * (feqb - fb[0]), kW0);
-  }
-  Unroll<0, 9>::run([&](auto kc) {
-    constexpr int I = 1 + 2 * decltype(kc)::value, J = I + 1;
-    constexpr float w = wgt(I);
-    const float cur = (float)dir_x(I) * ur[0] + (float)dir_y(I) * ur[1] + (float)dir_z(I) * ur[2];
-    const float cub = (float)dir_x(I) * ub[0] + (float)dir_y(I) * ub[1] + (float)dir_z(I) * ub[2];
-    const float wrr = w * rr, wrb = w * rb;
-    const float evr = wrr * (1.0f + 4.5f * cur * cur - 1.5f * usr), odr = wrr * (3.0f * cur);
-    const float evb = wrb * (1.0f + 4.5f * cub * cub - 1.5f * usb), odb = wrb * (3.0f * cub);
-    typename S::T* pi = dst + (long long)I * L.np + s;
-    typename S::T* pj = dst + (long long)J * L.np + s;
-    S::st(pi, fr[I] + omr * ((evr + odr) - fr[I]), w);
-    S::st(pj, fr[J] + omr * ((evr - odr) - fr[J]), w);
-    S::st(pi + cstride, fb[I] + omb * ((evb + odb) - fb[I]), w);
-    S::st(pj + cstride, fb[J] + omb * ((evb - odb) - fb[J]), w);
-  });
-}
-
-template <class S>
-__device__ __forceinline__ void store_plain(const LatDev& L, typename S::T* __restrict__ dst, int s,
-                                            const float (&fr)[Q], const float (&fb)[Q]) {
+__device__ __forceinline__ void store_site(const LatDev& L, typename S::T* __restrict__ dst, int s,
+                                           const float (&fr)[Q], const float (&fb)[Q]) {
   const long long cstride = (long long)Q * L.np;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
@@ -268,17 +219,123 @@ __device__ __forceinline__ void store_plain(const LatDev& L, typename S::T* __re
   }
 }
 
+// Momentum sum_i f_i e_i of one component.
+__device__ __forceinline__ void momentum(const float (&f)[Q], float (&m)[3]) {
+  m[0] = m[1] = m[2] = 0.f;
+  Unroll<1, Q>::run([&](auto ic) {
+    constexpr int I = decltype(ic)::value;
+    if (dir_x(I) > 0) m[0] += f[I];
+    if (dir_x(I) < 0) m[0] -= f[I];
+    if (dir_y(I) > 0) m[1] += f[I];
+    if (dir_y(I) < 0) m[1] -= f[I];
+    if (dir_z(I) > 0) m[2] += f[I];
+    if (dir_z(I) < 0) m[2] -= f[I];
+  });
+}
+
+// The collision arithmetic below spells out every rounding (__fmul_rn, __fmaf_rn,
+// ...) so that the compiler cannot contract it differently in different kernels:
+// every step kernel produces the same bits for the same state.
+
+// Common velocity u' = sum_c (m^c / tau_c) / sum_c (rho^c / tau_c) (Sec. II A: the
+// mass-weighted u_eq when tau_r = tau_b).
+__device__ __forceinline__ void common_velocity(const LatDev& L, float rr, float rb, const float (&mr)[3],
+                                                const float (&mb)[3], float (&up)[3]) {
+  const float omr = L.omega[0], omb = L.omega[1];
+  const float den = __fmaf_rn(rr, omr, __fmul_rn(rb, omb));
+  const float inv = den > 0.0f ? __fdiv_rn(1.0f, den) : 0.0f;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) up[d] = __fmul_rn(__fmaf_rn(mr[d], omr, __fmul_rn(mb[d], omb)), inv);
+}
+
+// c . u for a D3Q19 direction, summing the non-zero terms in x, y, z order.
+template <int I>
+__device__ __forceinline__ float cdot(const float (&u)[3]) {
+  constexpr int ex = dir_x(I), ey = dir_y(I), ez = dir_z(I);
+  float r = 0.0f;
+  bool first = true;
+  if (ex != 0) { r = ex > 0 ? u[0] : -u[0]; first = false; }
+  if (ey != 0) { r = first ? (ey > 0 ? u[1] : -u[1]) : (ey > 0 ? __fadd_rn(r, u[1]) : __fsub_rn(r, u[1])); first = false; }
+  if (ez != 0) { r = first ? (ez > 0 ? u[2] : -u[2]) : (ez > 0 ? __fadd_rn(r, u[2]) : __fsub_rn(r, u[2])); }
+  return r;
+}
+
+// Shifted-velocity BGK relaxation of component c at a fluid site (Eqs. (1)-(3)):
+// u_eq = u' + tau_c F^c / rho^c with F^c = -g Psi^c(x) a, a = sum_i w_i Psi^cbar(x + e_i) e_i.
+__device__ __forceinline__ void relax(const LatDev& L, int c, float (&f)[Q], float rho, float ps,
+                                      const float (&a)[3], const float (&up)[3]) {
+  const float om = c == 0 ? L.omega[0] : L.omega[1], tau = c == 0 ? L.tau[0] : L.tau[1];
+  const float sc = rho > 0.0f ? __fdiv_rn(tau, rho) : 0.0f;
+  const float gps = __fmul_rn(-L.G, ps);
+  float u[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) u[d] = __fmaf_rn(sc, __fmul_rn(gps, a[d]), up[d]);
+  const float usq = __fmaf_rn(u[0], u[0], __fmaf_rn(u[1], u[1], __fmul_rn(u[2], u[2])));
+  const float base = __fmaf_rn(-1.5f, usq, 1.0f);  // 1 - 1.5 u.u
+  // f^eq_i = w_i rho (1 + 3 c.u + 4.5 (c.u)^2 - 1.5 u.u); opposite directions share
+  // the even part and differ in the sign of the odd part.
+  f[0] = __fmaf_rn(om, __fsub_rn(__fmul_rn(__fmul_rn(kW0, rho), base), f[0]), f[0]);
+  Unroll<0, 9>::run([&](auto kc) {
+    constexpr int I = 1 + 2 * decltype(kc)::value, J = I + 1;
+    const float cu = cdot<I>(u);
+    const float wr = __fmul_rn(wgt(I), rho);
+    const float ev = __fmul_rn(wr, __fmaf_rn(__fmul_rn(4.5f, cu), cu, base));
+    const float od = __fmul_rn(wr, __fmul_rn(3.0f, cu));
+    f[I] = __fmaf_rn(om, __fsub_rn(__fadd_rn(ev, od), f[I]), f[I]);
+    f[J] = __fmaf_rn(om, __fsub_rn(__fsub_rn(ev, od), f[J]), f[J]);
+  });
+}
+
+// Shifted-velocity BGK collision of one fluid site, in place on fr/fb.
+// ar/ab: sum_i w_i Psi^{r|b}(x + e_i) e_i.
+__device__ __forceinline__ void collide(const LatDev& L, float (&fr)[Q], float (&fb)[Q], float rr, float rb, float psr,
+                                        float psb, const float (&ar)[3], const float (&ab)[3]) {
+  float mr[3], mb[3], up[3];
+  momentum(fr, mr);
+  momentum(fb, mb);
+  common_velocity(L, rr, rb, mr, mb, up);
+  relax(L, 0, fr, rr, psr, ab, up);
+  relax(L, 1, fb, rb, psb, ar, up);
+}
+
+// sum_i w_i Psi^c(x + e_i) e_i from a Psi ring; psi(c, plane slot, ly, lx).
+template <class PsiAt>
+__device__ __forceinline__ void force_sum(PsiAt psi, int c, int sm1, int s0, int sp1, int ly, int lx,
+                                          float (&a)[3]) {
+  a[0] = a[1] = a[2] = 0.f;
+  // opposite pairs (I, I+1): accumulate w_I (Psi(x+e_I) - Psi(x-e_I)) e_I
+  Unroll<0, 9>::run([&](auto kc) {
+    constexpr int I = 1 + 2 * decltype(kc)::value;
+    constexpr int ex = dir_x(I), ey = dir_y(I), ez = dir_z(I);
+    const int sa = ez > 0 ? sp1 : (ez < 0 ? sm1 : s0);
+    const int sb = ez > 0 ? sm1 : (ez < 0 ? sp1 : s0);
+    const float t = __fmul_rn(wgt(I), __fsub_rn(psi(c, sa, ly + ey, lx + ex), psi(c, sb, ly - ey, lx - ex)));
+    if (ex != 0) a[0] = ex > 0 ? __fadd_rn(a[0], t) : __fsub_rn(a[0], t);
+    if (ey != 0) a[1] = ey > 0 ? __fadd_rn(a[1], t) : __fsub_rn(a[1], t);
+    if (ez != 0) a[2] = ez > 0 ? __fadd_rn(a[2], t) : __fsub_rn(a[2], t);
+  });
+}
+
+template <class PsiAt>
+__device__ __forceinline__ void force_sums(PsiAt psi, int sm1, int s0, int sp1, int ly, int lx, float (&ar)[3],
+                                           float (&ab)[3]) {
+  force_sum(psi, 0, sm1, s0, sp1, ly, lx, ar);
+  force_sum(psi, 1, sm1, s0, sp1, ly, lx, ab);
+}
+
 // ------------------------------------------------------------------ fused step, one x-y tile column
 //
 // A CTA of TX*TY threads owns sites [x0, x0+TX) x [y0, y0+TY) and marches z over
 // [zb, ze). Psi of the tile plus a one-site halo lives in a 4-plane shared ring,
 // so the 18-neighbour force never reads Psi from HBM; halo densities are
 // recomputed from the neighbours' pulled populations (an L2 hit when the
-// neighbouring CTA is at the same plane). One barrier per plane: plane z+1 is
-// written while plane z-2's slot is free.
+// neighbouring CTA is at the same plane). The halo sites are spread over all
+// warps (a few lanes each) so every warp reaches the plane barrier with the
+// same amount of loading. One barrier per plane: plane z+1 is written while
+// plane z-2's slot is free.
 template <int TX, int TY, class S>
 struct Tile {
-  static constexpr int NT = TX * TY, RW = TX + 2, RH = TY + 2, NH = 2 * TX + 2 * RH;
+  static constexpr int NT = TX * TY, NW = NT / 32, RW = TX + 2, RH = TY + 2, NH = 2 * TX + 2 * RH;
   static_assert(NH <= NT, "halo slots exceed threads");
   static_assert(NT % 32 == 0, "whole warps");
 
@@ -298,7 +355,8 @@ struct Tile {
   __device__ __forceinline__ Tile(const LatDev& L_, Smem& sm_, const typename S::T* s_, typename S::T* d_)
       : L(L_), sm(sm_), src(s_), dst(d_), evap(0.0) {}
 
-  // Bind the CTA to tile column (bx, by).
+  // Bind the CTA to tile column (bx, by). Lanes past a ragged edge stage the
+  // wrapped site there (its Psi is the halo of the last real site).
   __device__ __forceinline__ void setup(int bx, int by) {
     const int tid = threadIdx.x;
     tx = tid % TX;
@@ -307,11 +365,13 @@ struct Tile {
     active = gx < L.nx && gy < L.ny;
     x = gx % L.nx;
     y = gy % L.ny;
-    has_halo = tid < NH;
-    if (tid < TX) { hlx = tid; hly = -1; }
-    else if (tid < 2 * TX) { hlx = tid - TX; hly = TY; }
-    else if (tid < 2 * TX + RH) { hlx = -1; hly = tid - 2 * TX - 1; }
-    else { hlx = TX; hly = tid - 2 * TX - RH - 1; }
+    // halo slot h = lane * NW + warp: warp w holds slots w, w + NW, ...
+    const int h = (tid & 31) * NW + (tid >> 5);
+    has_halo = h < NH;
+    if (h < TX) { hlx = h; hly = -1; }
+    else if (h < 2 * TX) { hlx = h - TX; hly = TY; }
+    else if (h < 2 * TX + RH) { hlx = -1; hly = h - 2 * TX - 1; }
+    else { hlx = TX; hly = h - 2 * TX - RH - 1; }
     hx = wrapi(bx * TX + hlx, L.nx);
     hy = wrapi(by * TY + hly, L.ny);
   }
@@ -358,56 +418,42 @@ struct Tile {
   // Collide plane z (values staged one plane earlier) and store f*.
   __device__ __forceinline__ void finish(int z, float (&fr)[Q], float (&fb)[Q], float rr, float rb, int cls) {
     if (!active || cls == SOLID) return;
-    const int s = x + L.nx * y + L.nxny * z;
+    const int s = x + L.nx * y + L.nxny * wrapi(z, L.nz);
     if (cls == SINK) {
       // Sinks are neither forced nor collided: they stream f^eq(rho_H, 0) and
       // f^eq(rho^r + rho^b - rho_H, 0) as they are.
 #pragma unroll
       for (int i = 0; i < Q; ++i) { fr[i] = rest_pop(i, rr); fb[i] = rest_pop(i, rb); }
-      store_plain<S>(L, dst, s, fr, fb);
-      return;
+    } else {
+      float ar[3], ab[3];
+      auto psi = [&](int c, int sl, int ly, int lx) { return sm.ring[c][sl][ly + 1][lx + 1]; };
+      force_sums(psi, (z - 1) & 3, z & 3, (z + 1) & 3, ty, tx, ar, ab);
+      const float psr = sm.ring[0][z & 3][ty + 1][tx + 1], psb = sm.ring[1][z & 3][ty + 1][tx + 1];
+      collide(L, fr, fb, rr, rb, psr, psb, ar, ab);
     }
-    const int s0 = z & 3, sm1 = (z - 1) & 3, sp1 = (z + 1) & 3;
-    float ar[3] = {0.f, 0.f, 0.f}, ab[3] = {0.f, 0.f, 0.f};
-    // opposite pairs (I, I+1): accumulate w_I (Psi(x+e_I) - Psi(x-e_I)) e_I
-    Unroll<0, 9>::run([&](auto kc) {
-      constexpr int I = 1 + 2 * decltype(kc)::value;
-      constexpr int ex = dir_x(I), ey = dir_y(I), ez = dir_z(I);
-      const int sa = ez > 0 ? sp1 : (ez < 0 ? sm1 : s0);
-      const int sb = ez > 0 ? sm1 : (ez < 0 ? sp1 : s0);
-      const float dr = sm.ring[0][sa][ty + 1 + ey][tx + 1 + ex] - sm.ring[0][sb][ty + 1 - ey][tx + 1 - ex];
-      const float db = sm.ring[1][sa][ty + 1 + ey][tx + 1 + ex] - sm.ring[1][sb][ty + 1 - ey][tx + 1 - ex];
-      constexpr float w = wgt(I);
-      if (ex != 0) { ar[0] += (float)ex * (w * dr); ab[0] += (float)ex * (w * db); }
-      if (ey != 0) { ar[1] += (float)ey * (w * dr); ab[1] += (float)ey * (w * db); }
-      if (ez != 0) { ar[2] += (float)ez * (w * dr); ab[2] += (float)ez * (w * db); }
-    });
-    const float psr = sm.ring[0][s0][ty + 1][tx + 1], psb = sm.ring[1][s0][ty + 1][tx + 1];
-    collide_store<S>(L, dst, s, fr, fb, rr, rb, psr, psb, ar, ab);
+    store_site<S>(L, dst, s, fr, fb);
   }
 
   // March planes [zb, ze) upward (down = false) or downward. Each plane is staged
-  // one plane ahead of its collision; the halo plane on the far side is staged
-  // for Psi only.
+  // one plane ahead of its collision; the halo plane on each end is staged for
+  // Psi only. One call site per phase keeps the kernel small.
   __device__ __forceinline__ void run(int zb, int ze, bool down) {
-    float ar_[Q], ab_[Q], br_[Q], bb_[Q];
-    float arr, arb, brr, brb;
-    int acl, bcl;
+    float cr[Q], cb[Q], nr[Q], nb[Q];
+    float crr = 0.f, crb = 0.f, nrr = 0.f, nrb = 0.f;
+    int ccl = SOLID, ncl = SOLID;
     const int d = down ? -1 : 1;
     const int first = down ? ze - 1 : zb;
     const int n = ze - zb;
-    auto own = [&](int p) { return p >= zb && p < ze; };
-    stage(first - d, false, ar_, ab_, arr, arb, acl);
-    stage(first, true, ar_, ab_, arr, arb, acl);
-    for (int k = 0; k < n; k += 2) {
-      const int z = first + d * k;
-      stage(z + d, own(z + d), br_, bb_, brr, brb, bcl);
+    for (int o = 0; o < n + 2; ++o) {
+      const int p = first + (o - 1) * d;
+      stage(p, o >= 1 && o <= n, nr, nb, nrr, nrb, ncl);
       __syncthreads();
-      finish(z, ar_, ab_, arr, arb, acl);
-      if (k + 1 >= n) break;
-      stage(z + 2 * d, own(z + 2 * d), ar_, ab_, arr, arb, acl);
-      __syncthreads();
-      finish(z + d, br_, bb_, brr, brb, bcl);
+      if (o >= 2) finish(p - d, cr, cb, crr, crb, ccl);
+#pragma unroll
+      for (int i = 0; i < Q; ++i) { cr[i] = nr[i]; cb[i] = nb[i]; }
+      crr = nrr;
+      crb = nrb;
+      ccl = ncl;
     }
   }
 

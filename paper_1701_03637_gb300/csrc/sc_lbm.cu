@@ -1,5 +1,5 @@
 // sc_lbm: C ABI and launches for the two-component Shan-Chen D3Q19 evaporation
-// step on sm_103a (arXiv:1701.03637, Sec. II). See include/sc_lbm.h for the
+// step on sm_103a (arXiv:1701.03637, Sec. II). include/sc_lbm.h documents the
 // contract of every entry point.
 #include <cuda_runtime.h>
 
@@ -35,20 +35,22 @@ int fail(int code, const char* fmt, ...) {
     if (e_ != cudaSuccess) return fail(SC_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
   } while (0)
 
+// Step kernel tile shapes (TX x TY sites per CTA).
 constexpr int kNumTiles = 4;
 constexpr int kTileX[kNumTiles] = {32, 32, 16, 8};
 constexpr int kTileY[kNumTiles] = {8, 4, 8, 4};
 
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
 
 // ------------------------------------------------------------------ kernels
 
-// Persistent fused step. The lattice is cut into tile columns of TX x TY sites
-// and z into nch chunks; item i = (chunk i / cols, column i % cols). CTA b takes
-// items b, b + G, b + 2G, ... so in every round the G resident CTAs work on
-// neighbouring columns of the same chunk in lock-step, and a column's halo and
-// shifted-pull sectors are read from DRAM once and then from L2 by its
-// neighbours. Chunks alternate their marching direction.
+// Persistent fused step (per-thread loads). The lattice is cut into tile columns
+// of TX x TY sites and z into nch chunks; item i = (chunk i / cols, column
+// i % cols). CTA b takes items b, b + G, b + 2G, ... so in every round the G
+// resident CTAs work on neighbouring columns of the same chunk in lock-step, and
+// a column's halo and shifted-pull sectors are read from DRAM once and then from
+// L2 by its neighbours. Chunks alternate their marching direction.
 template <int TX, int TY, class S>
 __global__ void __launch_bounds__(TX * TY, 2)
     k_step(const LatDev L, const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
@@ -72,15 +74,22 @@ __global__ void __launch_bounds__(TX * TY, 2)
   }
 }
 
-// Canonical state of every site (pull + sink), as densities and/or populations
-// for sites [s0, s1).
+__device__ __forceinline__ void site_of(const LatDev& L, long long s, int& x, int& y, int& z) {
+  x = (int)(s % L.nx);
+  y = (int)((s / L.nx) % L.ny);
+  z = (int)(s / ((long long)L.nx * L.ny));
+}
+
+// Canonical state (pull + sink) of compact sites [s0, s1), as densities and/or
+// populations in compact order.
 template <class S>
 __global__ void k_canonical(const LatDev L, const typename S::T* __restrict__ src, long long s0, long long s1,
                             float* __restrict__ rho_out, long long rho_stride, float* __restrict__ f_out,
                             long long f_stride) {
   for (long long s = s0 + blockIdx.x * (long long)blockDim.x + threadIdx.x; s < s1;
        s += (long long)gridDim.x * blockDim.x) {
-    const int x = (int)(s % L.nx), y = (int)((s / L.nx) % L.ny), z = (int)(s / L.nxny);
+    int x, y, z;
+    site_of(L, s, x, y, z);
     const int cls = site_class(L, x, y, z);
     float fr[Q], fb[Q], rr = 0.f, rb = 0.f;
     if (cls == SOLID) {
@@ -118,8 +127,9 @@ template <class S>
 __global__ void __launch_bounds__(kDiagThreads) k_diag(const LatDev L, const typename S::T* __restrict__ src,
                                                        int nsplit, double* __restrict__ part) {
   const int z = blockIdx.x, k = blockIdx.y;
-  const int per = (L.nxny + nsplit - 1) / nsplit;
-  const int b = k * per, e = min(b + per, L.nxny);
+  const int nxy = L.nx * L.ny;
+  const int per = (nxy + nsplit - 1) / nsplit;
+  const int b = k * per, e = min(b + per, nxy);
   // mass_r, mass_b, sum(rho_r - rho_b), pending evaporation, count(rho_r > rho_b),
   // non-finite flag, negative-complement flag
   constexpr int NF = 7;
@@ -167,8 +177,8 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag(const LatDev L, const typ
 
 // Initial / restored state: canonical populations of sites [s0, s1) from
 // (mode 0) an FP32 population slab, (mode 1) density fields, (mode 2) the seeded
-// film/droplet shape. Sinks are reset (evaporated mass not counted) and the
-// values are written to the slot the next pull reads them from.
+// film/droplet shape. Sinks are reset (evaporated mass not counted) and each
+// value is written to the slot the next pull of that site reads it from.
 struct ShapeDev {
   int shape, film_z;
   double cx, cy, cz, R2, hi, lo, amp;
@@ -190,7 +200,8 @@ __global__ void k_load(const LatDev L, typename S::T* __restrict__ dst, long lon
                        long long rho_stride, const ShapeDev sh, long long nsites) {
   for (long long s = s0 + blockIdx.x * (long long)blockDim.x + threadIdx.x; s < s1;
        s += (long long)gridDim.x * blockDim.x) {
-    const int x = (int)(s % L.nx), y = (int)((s / L.nx) % L.ny), z = (int)(s / L.nxny);
+    int x, y, z;
+    site_of(L, s, x, y, z);
     const int cls = site_class(L, x, y, z);
     if (cls == SOLID) continue;
     const long long o = s - s0;
@@ -230,14 +241,16 @@ __global__ void k_load(const LatDev L, typename S::T* __restrict__ dst, long lon
 #pragma unroll
       for (int i = 0; i < Q; ++i) { fr[i] = rest_pop(i, rr); fb[i] = rest_pop(i, rb); }
     }
-    // inverse of the pull: f_i(x) is read from x - e_i, or from (x, opp(i)) when
-    // x - e_i is solid.
-    const PullIdx P(L, x, y, z);
+    // inverse of the pull: f_i(x) is read from x - e_i (wrapped), or from (x, opp(i))
+    // when plane z - e_iz is solid.
     const long long cstride = (long long)Q * L.np;
     Unroll<0, Q>::run([&](auto ic) {
       constexpr int I = decltype(ic)::value;
-      int idx, d;
-      P.template at<I>(idx, d);
+      const int zs = wrapi(z - dir_z(I), L.nz);
+      const bool sol = dir_z(I) != 0 && solid_z(L, zs);
+      const int idx = sol ? x + L.nx * y + L.nxny * z
+                          : wrapi(x - dir_x(I), L.nx) + L.nx * wrapi(y - dir_y(I), L.ny) + L.nxny * zs;
+      const int d = sol ? opp(I) : I;
       typename S::T* p = dst + (long long)d * L.np + idx;
       S::st(p, fr[I], wgt(I));
       S::st(p + cstride, fb[I], wgt(I));
@@ -247,11 +260,19 @@ __global__ void k_load(const LatDev L, typename S::T* __restrict__ dst, long lon
 
 // ------------------------------------------------------------------ launch tables
 
+struct StepArgs {
+  LatDev L;
+  const void* src;
+  void* dst;
+  double* evap;
+  int cols_x, cols, nch, G;
+  cudaStream_t st;
+};
+
 template <int TX, int TY, class S>
-cudaError_t launch_step(const LatDev& L, const void* src, void* dst, double* evap, int cols_x, int cols, int nch,
-                        int G, cudaStream_t st) {
-  k_step<TX, TY, S><<<G, TX * TY, 0, st>>>(L, (const typename S::T*)src, (typename S::T*)dst, evap, cols_x, cols,
-                                            nch);
+cudaError_t launch_step(const StepArgs& a) {
+  k_step<TX, TY, S><<<a.G, TX * TY, 0, a.st>>>(a.L, (const typename S::T*)a.src, (typename S::T*)a.dst, a.evap,
+                                                a.cols_x, a.cols, a.nch);
   return cudaGetLastError();
 }
 
@@ -262,10 +283,10 @@ int occupancy_step() {
   return std::max(nb, 1);
 }
 
-using LaunchFn = cudaError_t (*)(const LatDev&, const void*, void*, double*, int, int, int, int, cudaStream_t);
+using LaunchFn = cudaError_t (*)(const StepArgs&);
 struct StepOps {
   LaunchFn launch;
-  int (*occupancy)();
+  int (*occupancy)();  // resident CTAs per SM
 };
 
 template <class S>
@@ -290,28 +311,11 @@ constexpr long long kMaxCtas = 4096;  // evaporated-mass slots, one per CTA of t
 
 size_t elem_size(int storage) { return storage == SC_STORAGE_F32 ? 4 : 2; }
 
-int validate(const sc_params* p) {
-  if (!p) return fail(SC_EINVAL, "params is NULL");
-  if (p->nx < 1 || p->ny < 1 || p->nz < 1) return fail(SC_EINVAL, "lattice extents must be >= 1");
-  if ((long long)p->nx * p->ny * p->nz > (1LL << 31) - 4096)
-    return fail(SC_EINVAL, "lattice too large: nx*ny*nz must stay below 2^31");
-  if (!(p->tau_r > 0.5) || !(p->tau_b > 0.5)) return fail(SC_EINVAL, "tau must exceed 1/2");
-  if (!std::isfinite(p->G) || !std::isfinite(p->rho_H)) return fail(SC_EINVAL, "G and rho_H must be finite");
-  if (p->geometry < 0 || p->geometry > 2) return fail(SC_EINVAL, "unknown geometry %d", p->geometry);
-  if (p->geometry == 1 && (p->sink_layers < 1 || p->sink_layers > p->nz))
-    return fail(SC_EINVAL, "sink_layers must be in [1, nz]");
-  if (p->geometry == 2 && !(p->R_H > 0)) return fail(SC_EINVAL, "R_H must be > 0");
-  if (p->wall_thickness < 0 || (p->wall_thickness > 0 && (p->wall_z0 < 0 || p->wall_z0 + p->wall_thickness > p->nz)))
-    return fail(SC_EINVAL, "wall slab must lie inside [0, nz)");
-  if (p->storage < 0 || p->storage > 2) return fail(SC_EINVAL, "unknown storage %d", p->storage);
-  if (p->tile < 0 || p->tile > kNumTiles) return fail(SC_EINVAL, "tile index out of range");
-  if (p->zchunk < 0) return fail(SC_EINVAL, "zchunk must be >= 0");
-  return SC_OK;
-}
-
 struct Layout {
   int tile, tx, ty, cols_x, cols;
-  long long np, nsites, units, nslots;
+  long long np;               // array stride (elements)
+  long long nsites, stage_n;  // sites; staging floats per component
+  long long units, nslots;
   int diag_nsplit;
   size_t off_pop[2], off_stage, off_evap, off_diag, total;
 };
@@ -324,26 +328,50 @@ int auto_tile(const sc_params* p) {
 
 Layout make_layout(const sc_params* p) {
   Layout l{};
+  const long long es = (long long)elem_size(p->storage);
   l.tile = p->tile > 0 ? p->tile - 1 : auto_tile(p);
   l.tx = kTileX[l.tile];
   l.ty = kTileY[l.tile];
   l.nsites = (long long)p->nx * p->ny * p->nz;
-  l.np = (l.nsites + 127) / 128 * 128;
+  l.np = round_up(l.nsites, 128 / es);  // each array starts 128-byte aligned
+  l.stage_n = round_up(l.nsites, 64);
   l.cols_x = (p->nx + l.tx - 1) / l.tx;
   l.cols = l.cols_x * ((p->ny + l.ty - 1) / l.ty);
   l.units = (long long)l.cols * p->nz;
   l.nslots = std::min(l.units, kMaxCtas);
   const long long per_plane = (long long)p->nx * p->ny;
   l.diag_nsplit = (int)std::max(1LL, std::min<long long>((4LL * 152 + p->nz - 1) / p->nz, (per_plane + 1023) / 1024));
-  const size_t pop = align256((size_t)2 * Q * l.np * elem_size(p->storage));
+  const size_t pop = align256((size_t)(2 * Q * l.np * es));
   size_t off = 0;
   l.off_pop[0] = off; off += pop;
   l.off_pop[1] = off; off += pop;
-  l.off_stage = off; off += align256((size_t)2 * l.np * sizeof(float));
+  l.off_stage = off; off += align256((size_t)2 * l.stage_n * sizeof(float));
   l.off_evap = off; off += align256((size_t)l.nslots * sizeof(double));
   l.off_diag = off; off += align256((size_t)p->nz * l.diag_nsplit * kDiagFields * sizeof(double));
   l.total = off;
   return l;
+}
+
+int validate(const sc_params* p) {
+  if (!p) return fail(SC_EINVAL, "params is NULL");
+  if (p->nx < 1 || p->ny < 1 || p->nz < 1) return fail(SC_EINVAL, "lattice extents must be >= 1");
+  if (!(p->tau_r > 0.5) || !(p->tau_b > 0.5) || !std::isfinite(p->tau_r) || !std::isfinite(p->tau_b))
+    return fail(SC_EINVAL, "tau must exceed 1/2");
+  if (!std::isfinite(p->G) || !std::isfinite(p->rho_H)) return fail(SC_EINVAL, "G and rho_H must be finite");
+  if (p->geometry < 0 || p->geometry > 2) return fail(SC_EINVAL, "unknown geometry %d", p->geometry);
+  if (p->geometry == 1 && (p->sink_layers < 1 || p->sink_layers > p->nz))
+    return fail(SC_EINVAL, "sink_layers must be in [1, nz]");
+  if (p->geometry == 2 && !(p->R_H > 0)) return fail(SC_EINVAL, "R_H must be > 0");
+  if (p->wall_thickness < 0 || (p->wall_thickness > 0 && (p->wall_z0 < 0 || p->wall_z0 + p->wall_thickness > p->nz)))
+    return fail(SC_EINVAL, "wall slab must lie inside [0, nz)");
+  if (p->storage < 0 || p->storage > 2) return fail(SC_EINVAL, "unknown storage %d", p->storage);
+  if (p->tile < 0 || p->tile > kNumTiles) return fail(SC_EINVAL, "tile index out of range");
+  if (p->zchunk < 0) return fail(SC_EINVAL, "zchunk must be >= 0");
+  if ((long long)p->nx > (1 << 20) || (long long)p->ny > (1 << 20) || (long long)p->nz > (1 << 20))
+    return fail(SC_EINVAL, "lattice extent too large");
+  if ((long long)p->nx * p->ny * p->nz > (1LL << 31) - 4096)
+    return fail(SC_EINVAL, "lattice too large: nx*ny*nz must stay below 2^31");
+  return SC_OK;
 }
 
 LatDev make_dev(const sc_params* p, const Layout& l) {
@@ -393,21 +421,21 @@ namespace {
 
 int launch_one(sc_lbm* h, cudaStream_t st) {
   const int src = h->cur, dst = 1 - h->cur;
-  cudaError_t e = step_ops(h->p.storage, h->lay.tile)
-                      .launch(h->L, h->pop(src), h->pop(dst), h->evap(), h->lay.cols_x, h->lay.cols, h->nch, h->grid,
-                              st);
+  StepArgs a{h->L, h->pop(src), h->pop(dst), h->evap(), h->lay.cols_x, h->lay.cols, h->nch, h->grid, st};
+  cudaError_t e = step_ops(h->p.storage, h->lay.tile).launch(a);
   if (e != cudaSuccess) return fail(SC_ECUDA, "step launch failed: %s", cudaGetErrorString(e));
   h->cur = dst;
   return SC_OK;
 }
 
+unsigned grid_for(long long n, int threads) {
+  return (unsigned)std::max(1LL, std::min<long long>((n + threads - 1) / threads, 152LL * 16));
+}
+
 template <class S>
 int launch_canonical(sc_lbm* h, long long s0, long long s1, float* rho, long long rs, float* f, long long fs) {
-  const long long n = s1 - s0;
-  const int threads = 256;
-  const long long blocks = std::min<long long>((n + threads - 1) / threads, 152LL * 16);
-  k_canonical<S><<<(unsigned)std::max(1LL, blocks), threads, 0, h->stream>>>(
-      h->L, (const typename S::T*)h->pop(h->cur), s0, s1, rho, rs, f, fs);
+  k_canonical<S><<<grid_for(s1 - s0, 256), 256, 0, h->stream>>>(h->L, (const typename S::T*)h->pop(h->cur), s0, s1,
+                                                                  rho, rs, f, fs);
   CK(cudaGetLastError());
   return SC_OK;
 }
@@ -423,12 +451,9 @@ int canonical(sc_lbm* h, long long s0, long long s1, float* rho, long long rs, f
 template <class S>
 int launch_load(sc_lbm* h, long long s0, long long s1, int mode, const float* f, long long fs, const float* rho,
                 long long rs, const ShapeDev& sh) {
-  const long long n = s1 - s0;
-  const int threads = 256;
-  const long long blocks = std::min<long long>((n + threads - 1) / threads, 152LL * 16);
   // the pull reads the current buffer, so the load writes it
-  k_load<S><<<(unsigned)std::max(1LL, blocks), threads, 0, h->stream>>>(
-      h->L, (typename S::T*)h->pop(h->cur), s0, s1, mode, f, fs, rho, rs, sh, h->lay.nsites);
+  k_load<S><<<grid_for(s1 - s0, 256), 256, 0, h->stream>>>(h->L, (typename S::T*)h->pop(h->cur), s0, s1, mode, f, fs,
+                                                            rho, rs, sh, h->lay.nsites);
   CK(cudaGetLastError());
   return SC_OK;
 }
@@ -458,8 +483,8 @@ int reset_counters(sc_lbm* h) {
   return SC_OK;
 }
 
-// Sites per slab so a slab's 2*19 FP32 populations fit the 2*np-float staging area.
-long long slab_sites(const sc_lbm* h) { return std::max<long long>(1, (2 * h->lay.np) / (2 * Q)); }
+// Sites per slab so a slab's 2*19 FP32 populations fit the staging area.
+long long slab_sites(const sc_lbm* h) { return std::max<long long>(1, (2 * h->lay.stage_n) / (2 * Q)); }
 
 }  // namespace
 
@@ -492,9 +517,12 @@ int sc_lbm_required_bytes(const sc_params* p, size_t* bytes) {
   return SC_OK;
 }
 
-static int create_common(const sc_params* p, void* stream, void* buf, size_t bytes, bool owns, sc_lbm** out) {
+static int create_common(const sc_params* p, void* stream, void* buf, bool owns, sc_lbm** out) {
   sc_lbm* h = new (std::nothrow) sc_lbm();
-  if (!h) return fail(SC_ENOMEM, "host allocation failed");
+  if (!h) {
+    if (owns) cudaFree(buf);
+    return fail(SC_ENOMEM, "host allocation failed");
+  }
   h->p = *p;
   h->lay = make_layout(p);
   h->L = make_dev(p, h->lay);
@@ -502,23 +530,18 @@ static int create_common(const sc_params* p, void* stream, void* buf, size_t byt
   h->base = (char*)buf;
   h->owns = owns;
   h->cur = 0;
-  h->graph = nullptr;
-  h->graph_len = 0;
-  h->graph_cur = 0;
-  // persistent grid: every resident CTA slot, or one CTA per zchunk planes of work
   int dev = 0, sms = 1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) {
-    if (owns) cudaFree(buf);
-    delete h;
+    sc_lbm_destroy(h);
     return fail(SC_ECUDA, "device query failed: %s", cudaGetErrorString(e));
   }
   // Persistent grid of every resident CTA slot. The z chunk count trades rounds
   // (ceil(items / G)) against the two extra planes each item stages; a caller
   // zchunk > 0 fixes the chunk length instead.
-  const long long slots = std::min<long long>((long long)sms * step_ops(p->storage, h->lay.tile).occupancy(),
-                                              h->lay.nslots);
+  const int occ = step_ops(p->storage, h->lay.tile).occupancy();
+  const long long slots = std::min<long long>((long long)sms * occ, h->lay.nslots);
   const long long cols = h->lay.cols;
   long long best_nch = 1;
   if (p->zchunk > 0) {
@@ -536,12 +559,14 @@ static int create_common(const sc_params* p, void* stream, void* buf, size_t byt
   e = cudaMallocHost((void**)&h->h_diag, sizeof(double) * p->nz * h->lay.diag_nsplit * kDiagFields);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&h->h_evap, sizeof(double) * h->lay.nslots);
   if (e != cudaSuccess) {
-    if (h->h_diag) cudaFreeHost(h->h_diag);
-    if (owns) cudaFree(buf);
-    delete h;
+    sc_lbm_destroy(h);
     return fail(SC_ENOMEM, "pinned host allocation failed: %s", cudaGetErrorString(e));
   }
-  (void)bytes;
+  e = cudaMemsetAsync(buf, 0, h->lay.off_stage, h->stream);
+  if (e != cudaSuccess) {
+    sc_lbm_destroy(h);
+    return fail(SC_ECUDA, "cudaMemsetAsync failed: %s", cudaGetErrorString(e));
+  }
   int rc = reset_counters(h);
   if (rc) { sc_lbm_destroy(h); return rc; }
   *out = h;
@@ -556,7 +581,7 @@ int sc_lbm_create(const sc_params* p, void* stream, sc_lbm** out) {
   void* buf = nullptr;
   cudaError_t e = cudaMalloc(&buf, l.total);
   if (e != cudaSuccess) return fail(SC_ENOMEM, "cudaMalloc(%zu) failed: %s", l.total, cudaGetErrorString(e));
-  return create_common(p, stream, buf, l.total, true, out);
+  return create_common(p, stream, buf, true, out);
 }
 
 int sc_lbm_create_ext(const sc_params* p, void* stream, void* buf, size_t bytes, sc_lbm** out) {
@@ -566,7 +591,7 @@ int sc_lbm_create_ext(const sc_params* p, void* stream, void* buf, size_t bytes,
   if (((uintptr_t)buf & 255) != 0) return fail(SC_EINVAL, "device buffer must be 256-byte aligned");
   const Layout l = make_layout(p);
   if (bytes < l.total) return fail(SC_ENOMEM, "device buffer has %zu bytes, needs %zu", bytes, l.total);
-  return create_common(p, stream, buf, bytes, false, out);
+  return create_common(p, stream, buf, false, out);
 }
 
 void sc_lbm_destroy(sc_lbm* h) {
@@ -610,11 +635,10 @@ int sc_lbm_init_fields(sc_lbm* h, const float* rr, const float* rb) {
   const long long n = h->lay.nsites;
   float* st = h->stage();
   CK(cudaMemcpyAsync(st, rr, sizeof(float) * n, cudaMemcpyHostToDevice, h->stream));
-  CK(cudaMemcpyAsync(st + h->lay.np, rb, sizeof(float) * n, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(st + h->lay.stage_n, rb, sizeof(float) * n, cudaMemcpyHostToDevice, h->stream));
   ShapeDev sh{};
-  int rc = load(h, 0, n, 1, nullptr, 0, st, h->lay.np, sh);
-  if (rc) return rc;
-  rc = reset_counters(h);
+  int rc = load(h, 0, n, 1, nullptr, 0, st, h->lay.stage_n, sh);
+  if (!rc) rc = reset_counters(h);
   if (rc) return rc;
   CK(cudaStreamSynchronize(h->stream));
   return SC_OK;
@@ -672,20 +696,21 @@ int sc_lbm_step(sc_lbm* h, int64_t nsteps) {
 
 int sc_lbm_read_fields_device(sc_lbm* h, float* rr, float* rb) {
   if (!h || !rr || !rb) return fail(SC_EINVAL, "NULL argument");
-  int rc = canonical(h, 0, h->lay.nsites, h->stage(), h->lay.np, nullptr, 0);
+  int rc = canonical(h, 0, h->lay.nsites, h->stage(), h->lay.stage_n, nullptr, 0);
   if (rc) return rc;
   CK(cudaMemcpyAsync(rr, h->stage(), sizeof(float) * h->lay.nsites, cudaMemcpyDeviceToDevice, h->stream));
-  CK(cudaMemcpyAsync(rb, h->stage() + h->lay.np, sizeof(float) * h->lay.nsites, cudaMemcpyDeviceToDevice,
+  CK(cudaMemcpyAsync(rb, h->stage() + h->lay.stage_n, sizeof(float) * h->lay.nsites, cudaMemcpyDeviceToDevice,
                      h->stream));
   return SC_OK;
 }
 
 int sc_lbm_read_fields(sc_lbm* h, float* rr, float* rb) {
   if (!h || !rr || !rb) return fail(SC_EINVAL, "NULL argument");
-  int rc = canonical(h, 0, h->lay.nsites, h->stage(), h->lay.np, nullptr, 0);
+  int rc = canonical(h, 0, h->lay.nsites, h->stage(), h->lay.stage_n, nullptr, 0);
   if (rc) return rc;
   CK(cudaMemcpyAsync(rr, h->stage(), sizeof(float) * h->lay.nsites, cudaMemcpyDeviceToHost, h->stream));
-  CK(cudaMemcpyAsync(rb, h->stage() + h->lay.np, sizeof(float) * h->lay.nsites, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(rb, h->stage() + h->lay.stage_n, sizeof(float) * h->lay.nsites, cudaMemcpyDeviceToHost,
+                     h->stream));
   CK(cudaStreamSynchronize(h->stream));
   return SC_OK;
 }
@@ -753,11 +778,12 @@ int sc_lbm_profile(sc_lbm* h, double* phi) {
   int rc = run_diag(h);
   if (rc) return rc;
   const int ns = h->lay.diag_nsplit;
+  const double nxy = (double)h->p.nx * h->p.ny;
   for (int z = 0; z < h->p.nz; ++z) {
     if (h->L.wall_z0 <= z && z < h->L.wall_z1) { phi[z] = NAN; continue; }
     double acc = 0.0;
     for (int k = 0; k < ns; ++k) acc += h->h_diag[((size_t)z * ns + k) * kDiagFields + 2];
-    phi[z] = acc / (double)h->L.nxny;
+    phi[z] = acc / nxy;
   }
   return SC_OK;
 }
@@ -768,6 +794,7 @@ int sc_lbm_diagnostics(sc_lbm* h, sc_diag* d) {
   if (rc) return rc;
   std::memset(d, 0, sizeof(*d));
   const int nz = h->p.nz, ns = h->lay.diag_nsplit;
+  const double nxy = (double)h->p.nx * h->p.ny;
   std::vector<double> phi(nz);
   double pending = 0.0, count = 0.0, nonfinite = 0.0, sinkneg = 0.0;
   for (int z = 0; z < nz; ++z) {
@@ -782,7 +809,7 @@ int sc_lbm_diagnostics(sc_lbm* h, sc_diag* d) {
       nonfinite = std::max(nonfinite, q[5]);
       sinkneg = std::max(sinkneg, q[6]);
     }
-    phi[z] = (h->L.wall_z0 <= z && z < h->L.wall_z1) ? NAN : pz / (double)h->L.nxny;
+    phi[z] = (h->L.wall_z0 <= z && z < h->L.wall_z1) ? NAN : pz / nxy;
   }
   double cum = 0.0;
   for (long long k = 0; k < h->lay.nslots; ++k) cum += h->h_evap[k];
