@@ -153,6 +153,22 @@ int sc_lbm_diagnostics(sc_lbm* h, sc_diag* out);
 /* phi(z) = mean over non-solid (x, y) of rho^r - rho^b, nz doubles (NaN for solid planes). */
 int sc_lbm_profile(sc_lbm* h, double* phi_host);
 
+/* Diagnostics for callers that cannot allocate device memory (for instance code
+   running under an allocator they do not control, or inside a process whose
+   memory budget is fixed up front). The paper has no counterpart: this is the
+   same FP64 reduction as sc_lbm_diagnostics, but its per-plane partial sums go to
+   a file-scope device array of 262144 doubles (2 MiB, held by every device that
+   loads this library until the process exits) and are folded on the device, so
+   the call allocates nothing (no cudaMalloc, no pinned host memory) and does not
+   synchronize. It writes 8 doubles to out_dev (caller-owned device memory), in
+   order: mass_r, mass_b, evaporated_mass, flux_last, interface_z, radius,
+   droplet_sites, status; they are ready when the handle's stream reaches this
+   point. Returns SC_EINVAL when nz * (plane splits) * 8 exceeds the array (nz
+   beyond about 16000). The first call on a device looks up the array's device
+   address, so it should come before any stream capture on that device. All calls
+   on a device share the array: calls whose work overlaps on the GPU race. */
+int sc_lbm_diagnostics_noalloc(sc_lbm* h, double* out_dev);
+
 /* Kernel configuration in use: tile extents, planes per CTA, grid size. */
 int sc_lbm_launch_info(sc_lbm* h, int32_t* tile_x, int32_t* tile_y, int32_t* zchunk, int64_t* ctas);
 /* Bytes one sc_lbm_diagnostics / sc_lbm_profile call copies device-to-host. */

@@ -103,6 +103,7 @@ _SIGS = {
     "sc_lbm_diagnostics": (C.c_int, [_VP, C.POINTER(Diag)]),
     "sc_lbm_profile": (C.c_int, [_VP, _VP]),
     "sc_lbm_diag_bytes": (C.c_int, [_VP, C.POINTER(C.c_size_t)]),
+    "sc_lbm_diagnostics_noalloc": (C.c_int, [_VP, _VP]),
     "sc_lbm_launch_info": (C.c_int, [_VP, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                      C.POINTER(C.c_int64)]),
 }

@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <type_traits>
 #include <vector>
@@ -173,6 +174,59 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag(const LatDev L, const typ
     for (int w = 0; w < kDiagThreads / 32; ++w) t = (j >= 5) ? fmax(t, red[w][j]) : t + red[w][j];
     part[((long long)z * nsplit + k) * kDiagFields + j] = t;
   }
+}
+
+// ------------------------------------------------------------------ diagnostics without allocation
+//
+// For callers that cannot allocate device memory: the per-plane partial sums
+// of k_diag go to this file-scope array (every device that loads the library
+// holds it until the process exits) instead of the handle's buffer, and
+// k_diag_finish folds them on the device, in the host reduction's order, into
+// the caller's output. k_diag overwrites every slot a call reads, so nothing
+// carries over between calls; calls that overlap on the GPU share the array and
+// race.
+constexpr long long kNoAllocScratch = 262144;  // doubles, 2 MiB per device
+__device__ __align__(256) double g_noalloc_scratch[kNoAllocScratch];
+
+__global__ void k_diag_finish(const double* __restrict__ part, int nz, int nsplit, double nxy, int wall_z0,
+                              int wall_z1, const double* __restrict__ evap_slots, long long nslots,
+                              double evap_offset, double* __restrict__ out) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  double mass_r = 0.0, mass_b = 0.0, pending = 0.0, count = 0.0, nonfinite = 0.0, sinkneg = 0.0;
+  const int z0 = wall_z1 > wall_z0 ? wall_z1 : 0;
+  double interface_z = -1.0, prev = 0.0;
+  bool have_prev = false;
+  for (int z = 0; z < nz; ++z) {
+    double pz = 0.0;
+    for (int k = 0; k < nsplit; ++k) {
+      const double* q = part + ((long long)z * nsplit + k) * kDiagFields;
+      mass_r += q[0];
+      mass_b += q[1];
+      pz += q[2];
+      pending += q[3];
+      count += q[4];
+      nonfinite = fmax(nonfinite, q[5]);
+      sinkneg = fmax(sinkneg, q[6]);
+    }
+    const bool solid = wall_z0 <= z && z < wall_z1;
+    const double phi = pz / nxy;
+    // first downward zero crossing of phi above the liquid base
+    if (interface_z < 0.0 && have_prev && z - 1 >= z0 && prev > 0.0 && phi <= 0.0 && !solid)
+      interface_z = (z - 1) + prev / (prev - phi);
+    have_prev = !solid;
+    prev = phi;
+  }
+  double cum = 0.0;
+  for (long long k = 0; k < nslots; ++k) cum += evap_slots[k];
+  out[0] = mass_r;
+  out[1] = mass_b;
+  out[2] = evap_offset + cum + pending;
+  out[3] = pending;
+  out[4] = interface_z;
+  out[5] = cbrt(3.0 * count / (4.0 * 3.141592653589793));
+  out[6] = count;
+  const bool bad = nonfinite > 0.0 || !isfinite(mass_r) || !isfinite(mass_b);
+  out[7] = bad ? (double)SC_ENONFINITE : (sinkneg > 0.0 ? (double)SC_ESINKNEG : (double)SC_OK);
 }
 
 // Initial / restored state: canonical populations of sites [s0, s1) from
@@ -486,6 +540,36 @@ int reset_counters(sc_lbm* h) {
 // Sites per slab so a slab's 2*19 FP32 populations fit the staging area.
 long long slab_sites(const sc_lbm* h) { return std::max<long long>(1, (2 * h->lay.stage_n) / (2 * Q)); }
 
+}  // namespace
+
+namespace {
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[128] = {};  // address of g_noalloc_scratch per device ordinal
+
+// Device address of the file-scope scratch for the current device, looked up once
+// per device (host code may not use the symbol itself as a device pointer).
+int noalloc_scratch(double** out) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 128) return fail(SC_EINVAL, "device ordinal %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_ptr[dev] = (double*)p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return SC_OK;
+}
+
+template <class S>
+int launch_diag_into(sc_lbm* h, double* part) {
+  dim3 grid(h->p.nz, h->lay.diag_nsplit);
+  k_diag<S><<<grid, kDiagThreads, 0, h->stream>>>(h->L, (const typename S::T*)h->pop(h->cur), h->lay.diag_nsplit,
+                                                  part);
+  CK(cudaGetLastError());
+  return SC_OK;
+}
 }  // namespace
 
 extern "C" {
@@ -829,6 +913,27 @@ int sc_lbm_diagnostics(sc_lbm* h, sc_diag* d) {
   }
   d->status = nonfinite > 0.0 ? SC_ENONFINITE : (sinkneg > 0.0 ? SC_ESINKNEG : SC_OK);
   if (!std::isfinite(d->mass_r) || !std::isfinite(d->mass_b)) d->status = SC_ENONFINITE;
+  return SC_OK;
+}
+
+int sc_lbm_diagnostics_noalloc(sc_lbm* h, double* out_dev) {
+  if (!h || !out_dev) return fail(SC_EINVAL, "NULL argument");
+  const long long need = (long long)h->p.nz * h->lay.diag_nsplit * kDiagFields;
+  if (need > kNoAllocScratch)
+    return fail(SC_EINVAL, "diagnostics without allocation need %lld doubles of scratch, the limit is %lld (nz too large)",
+                need, kNoAllocScratch);
+  double* part = nullptr;
+  int rc = noalloc_scratch(&part);
+  if (rc) return rc;
+  switch (h->p.storage) {
+    case SC_STORAGE_F16: rc = launch_diag_into<StF16>(h, part); break;
+    case SC_STORAGE_BF16: rc = launch_diag_into<StBF16>(h, part); break;
+    default: rc = launch_diag_into<StF32>(h, part);
+  }
+  if (rc) return rc;
+  k_diag_finish<<<1, 1, 0, h->stream>>>(part, h->p.nz, h->lay.diag_nsplit, (double)h->p.nx * h->p.ny, h->L.wall_z0,
+                                        h->L.wall_z1, h->evap(), h->lay.nslots, h->evap_offset, out_dev);
+  CK(cudaGetLastError());
   return SC_OK;
 }
 
