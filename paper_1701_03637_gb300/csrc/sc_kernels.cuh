@@ -58,30 +58,62 @@ struct LatDev {
   float omega[2], tau[2];  // 1/tau and tau per component
   float G, rhoH;           // g of Eq. (3); imposed rho^r at sinks
   double rhoH_mass;        // exact sum of the reset r populations fl(w_i rho_H)
-  int geometry, sink_z0, sink_layers;
+  int geometry, sink_z0, sink_layers;  // sink_z0 in [0, nz)
   double scx, scy, scz, RH2;
   int wall_z0, wall_z1;    // solid slab [wall_z0, wall_z1)
 };
 
 // ------------------------------------------------------------------ storage types
+// ld: a population from global memory. pull_async: start a 4-byte asynchronous
+// copy (cp.async, cached in L1) of the word holding a population into shared
+// memory and return which half of the word it is (16-bit types). word: the
+// population from such a word.
+__device__ __forceinline__ void cp_async4(uint32_t* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
 struct StF32 {
   using T = float;
   static __device__ __forceinline__ float ld(const T* p, float) { return __ldg(p); }
   static __device__ __forceinline__ float cv(T v, float) { return v; }
   static __device__ __forceinline__ void st(T* p, float v, float) { *p = v; }
+  static __device__ __forceinline__ uint32_t pull_async(uint32_t* sm, const T* p) {
+    cp_async4(sm, p);
+    return 0u;
+  }
+  static __device__ __forceinline__ float word(uint32_t w, uint32_t, float) { return __uint_as_float(w); }
 };
 // FP16 / BF16 offsets h = f - w_i * rho0 (rho0 = 1), round to nearest even.
+// Arrays hold an even number of elements, so the aligned word of any element
+// lies inside its array.
+template <class Half>
+__device__ __forceinline__ uint32_t pull_async16(uint32_t* sm, const Half* p) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+  cp_async4(sm, reinterpret_cast<const void*>(a & ~uintptr_t(3)));
+  return (uint32_t)(a >> 1) & 1u;
+}
 struct StF16 {
   using T = __half;
   static __device__ __forceinline__ float ld(const T* p, float w) { return w + __half2float(__ldg(p)); }
   static __device__ __forceinline__ float cv(T v, float w) { return w + __half2float(v); }
   static __device__ __forceinline__ void st(T* p, float v, float w) { *p = __float2half_rn(v - w); }
+  static __device__ __forceinline__ uint32_t pull_async(uint32_t* sm, const T* p) { return pull_async16(sm, p); }
+  static __device__ __forceinline__ float word(uint32_t w, uint32_t hi, float wt) {
+    return wt + __half2float(__ushort_as_half((unsigned short)(hi ? w >> 16 : w & 0xffffu)));
+  }
 };
 struct StBF16 {
   using T = __nv_bfloat16;
   static __device__ __forceinline__ float ld(const T* p, float w) { return w + __bfloat162float(__ldg(p)); }
   static __device__ __forceinline__ float cv(T v, float w) { return w + __bfloat162float(v); }
   static __device__ __forceinline__ void st(T* p, float v, float w) { *p = __float2bfloat16_rn(v - w); }
+  static __device__ __forceinline__ uint32_t pull_async(uint32_t* sm, const T* p) { return pull_async16(sm, p); }
+  static __device__ __forceinline__ float word(uint32_t w, uint32_t hi, float wt) {
+    return wt + __bfloat162float(__ushort_as_bfloat16((unsigned short)(hi ? w >> 16 : w & 0xffffu)));
+  }
 };
 
 __host__ __device__ __forceinline__ int wrapi(int v, int n) {
@@ -96,7 +128,10 @@ __device__ __forceinline__ bool solid_z(const LatDev& L, int z) { return z >= L.
 // plain host evaluation.
 __device__ __forceinline__ int site_class(const LatDev& L, int x, int y, int z) {
   if (solid_z(L, z)) return SOLID;
-  if (L.geometry == 1) return wrapi(z - L.sink_z0, L.nz) < L.sink_layers ? SINK : FLUID;
+  if (L.geometry == 1) {
+    const int dz = z - L.sink_z0;  // sink_z0 in [0, nz), z in [0, nz)
+    return (dz < 0 ? dz + L.nz : dz) < L.sink_layers ? SINK : FLUID;
+  }
   if (L.geometry == 2) {
     const double dx = (double)x - L.scx, dy = (double)y - L.scy, dz = (double)z - L.scz;
     const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
@@ -158,6 +193,24 @@ __device__ __forceinline__ void pull_full(const LatDev& L, const typename S::T* 
     fr[I] = S::ld(p, wgt(I));
     fb[I] = S::ld(p + cstride, wgt(I));
   });
+}
+
+// Asynchronous form of pull_full: population (c, i) goes to sm[(c Q + i) stride];
+// bit i of the result says which half of the word holds direction i.
+template <class S>
+__device__ __forceinline__ uint32_t pull_async(const LatDev& L, const typename S::T* __restrict__ src,
+                                               const PullIdx& P, uint32_t* sm, int stride) {
+  const long long cstride = (long long)Q * L.np;
+  uint32_t hi = 0u;
+  Unroll<0, Q>::run([&](auto ic) {
+    constexpr int I = decltype(ic)::value;
+    int idx, d;
+    P.template at<I>(idx, d);
+    const typename S::T* p = src + (long long)d * L.np + idx;
+    hi |= S::pull_async(sm + I * stride, p) << I;
+    S::pull_async(sm + (Q + I) * stride, p + cstride);
+  });
+  return hi;
 }
 
 // Same loads, summed in the same order as sum19() so both give identical bits.
@@ -329,19 +382,30 @@ __device__ __forceinline__ void force_sums(PsiAt psi, int sm1, int s0, int sp1, 
 // [zb, ze). Psi of the tile plus a one-site halo lives in a 4-plane shared ring,
 // so the 18-neighbour force never reads Psi from HBM; halo densities are
 // recomputed from the neighbours' pulled populations (an L2 hit when the
-// neighbouring CTA is at the same plane). The halo sites are spread over all
-// warps (a few lanes each) so every warp reaches the plane barrier with the
-// same amount of loading. One barrier per plane: plane z+1 is written while
-// plane z-2's slot is free.
+// neighbouring CTA is at the same plane). Halo slot h belongs to thread h: the
+// two halo rows each fill a warp with contiguous sites, so their pulls coalesce
+// like the interior's (spreading them over all warps instead made every halo
+// load touch a sector per lane). One barrier per plane: plane z+1 is written
+// while plane z-2's slot is free.
+//
+// The pulls of the next plane are asynchronous copies into shared slots that
+// belong to the issuing thread alone (its site's 38 populations, and its halo
+// site's), started as soon as the current plane has been read out of them, so
+// their latency overlaps the collision of the previous plane without holding
+// registers. Only the thread that issued a copy reads its slot, so a wait on its
+// own copies is the only synchronisation the slots need.
 template <int TX, int TY, class S>
 struct Tile {
   static constexpr int NT = TX * TY, NW = NT / 32, RW = TX + 2, RH = TY + 2, NH = 2 * TX + 2 * RH;
+  static constexpr int HS = (NH + 31) / 32 * 32;  // halo slot stride
   static_assert(NH <= NT, "halo slots exceed threads");
   static_assert(NT % 32 == 0, "whole warps");
 
   struct Smem {
     float ring[2][4][RH][RW];
-    double red[NT / 32];
+    double red[NW];
+    uint32_t fin[2 * Q][NT];       // pulled populations of the own site, [c Q + i][thread]
+    uint32_t fh[2 * Q][HS];        // pulled populations of the halo site, [c Q + i][thread]
   };
 
   const LatDev& L;
@@ -355,6 +419,10 @@ struct Tile {
   __device__ __forceinline__ Tile(const LatDev& L_, Smem& sm_, const typename S::T* s_, typename S::T* d_)
       : L(L_), sm(sm_), src(s_), dst(d_), evap(0.0) {}
 
+  __device__ __forceinline__ int wrapz(int z) const { return z < 0 ? z + L.nz : (z >= L.nz ? z - L.nz : z); }
+  __device__ __forceinline__ uint32_t* own_slot() { return &sm.fin[0][threadIdx.x]; }
+  __device__ __forceinline__ uint32_t* halo_slot() { return &sm.fh[0][threadIdx.x]; }
+
   // Bind the CTA to tile column (bx, by). Lanes past a ragged edge stage the
   // wrapped site there (its Psi is the halo of the last real site).
   __device__ __forceinline__ void setup(int bx, int by) {
@@ -365,8 +433,8 @@ struct Tile {
     active = gx < L.nx && gy < L.ny;
     x = gx % L.nx;
     y = gy % L.ny;
-    // halo slot h = lane * NW + warp: warp w holds slots w, w + NW, ...
-    const int h = (tid & 31) * NW + (tid >> 5);
+    // halo slot h = tid: top row, bottom row, left column, right column
+    const int h = tid;
     has_halo = h < NH;
     if (h < TX) { hlx = h; hly = -1; }
     else if (h < 2 * TX) { hlx = h - TX; hly = TY; }
@@ -376,18 +444,34 @@ struct Tile {
     hy = wrapi(by * TY + hly, L.ny);
   }
 
-  // Pull plane p (the interior site into fr/fb, the halo slot as sums), apply
-  // the sink, and publish Psi to ring slot p & 3.
-  __device__ __forceinline__ void stage(int p, bool own, float (&fr)[Q], float (&fb)[Q], float& rr, float& rb,
-                                        int& cls) {
-    const int zp = wrapi(p, L.nz), slot = p & 3;
+  // Start the pulls of plane p (p in [-1, nz]) for the own site and the halo site.
+  __device__ __forceinline__ void issue(int p, int& cls, uint32_t& hi, int& hcl, uint32_t& hhi) {
+    const int zp = wrapz(p);
     cls = site_class(L, x, y, zp);
+    if (cls != SOLID) hi = pull_async<S>(L, src, PullIdx(L, x, y, zp), own_slot(), NT);
+    if (has_halo) {
+      hcl = site_class(L, hx, hy, zp);
+      if (hcl != SOLID) hhi = pull_async<S>(L, src, PullIdx(L, hx, hy, zp), halo_slot(), HS);
+    }
+    cp_async_commit();
+  }
+
+  // Read plane p out of the slots (after the wait): the own site into fr/fb, the
+  // halo site as sums; apply the sink and publish Psi to ring slot p & 3.
+  __device__ __forceinline__ void take(int p, bool own, int cls, uint32_t hi, int hcl, uint32_t hhi,
+                                       float (&fr)[Q], float (&fb)[Q], float& rr, float& rb) {
+    const int slot = p & 3;
     float pr = 0.0f, pb = 0.0f;
     if (cls == SOLID) {
       rr = rb = 0.0f;
     } else {
-      const PullIdx P(L, x, y, zp);
-      pull_full<S>(L, src, P, fr, fb);
+      const uint32_t* w = own_slot();
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        const uint32_t h = (hi >> i) & 1u;
+        fr[i] = S::word(w[i * NT], h, wgt(i));
+        fb[i] = S::word(w[(Q + i) * NT], h, wgt(i));
+      }
       rr = sum19(fr);
       rb = sum19(fb);
       if (cls == SINK) {
@@ -400,13 +484,18 @@ struct Tile {
     sm.ring[0][slot][ty + 1][tx + 1] = pr;
     sm.ring[1][slot][ty + 1][tx + 1] = pb;
     if (has_halo) {
-      const int hc = site_class(L, hx, hy, zp);
       float hpr = 0.0f, hpb = 0.0f;
-      if (hc != SOLID) {
-        const PullIdx P(L, hx, hy, zp);
-        float hrr, hrb;
-        pull_sums<S>(L, src, P, hrr, hrb);
-        if (hc == SINK) sink_densities(L, hrr, hrb);
+      if (hcl != SOLID) {
+        const uint32_t* w = halo_slot();
+        // summed in sum19's order, so the halo Psi has the owner's bits
+        float hrr = 0.0f, hrb = 0.0f;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+          const uint32_t h = (hhi >> i) & 1u;
+          hrr = hrr + S::word(w[i * HS], h, wgt(i));
+          hrb = hrb + S::word(w[(Q + i) * HS], h, wgt(i));
+        }
+        if (hcl == SINK) sink_densities(L, hrr, hrb);
         hpr = psi_of(hrr);
         hpb = psi_of(hrb);
       }
@@ -415,10 +504,10 @@ struct Tile {
     }
   }
 
-  // Collide plane z (values staged one plane earlier) and store f*.
+  // Collide plane z (in [0, nz); read out one plane earlier) and store f*.
   __device__ __forceinline__ void finish(int z, float (&fr)[Q], float (&fb)[Q], float rr, float rb, int cls) {
     if (!active || cls == SOLID) return;
-    const int s = x + L.nx * y + L.nxny * wrapi(z, L.nz);
+    const int s = x + L.nx * y + L.nxny * z;
     if (cls == SINK) {
       // Sinks are neither forced nor collided: they stream f^eq(rho_H, 0) and
       // f^eq(rho^r + rho^b - rho_H, 0) as they are.
@@ -434,26 +523,33 @@ struct Tile {
     store_site<S>(L, dst, s, fr, fb);
   }
 
-  // March planes [zb, ze) upward (down = false) or downward. Each plane is staged
-  // one plane ahead of its collision; the halo plane on each end is staged for
-  // Psi only. One call site per phase keeps the kernel small.
+  // March planes [zb, ze) upward (down = false) or downward. Plane p is read out
+  // of the slots at step o, its successor's pulls are started, and after the
+  // barrier plane p - d (whose Psi neighbours are now all in the ring) collides.
+  // The halo plane on each end is staged for Psi only. The ring slot of plane
+  // p is p & 3 for p = -1 too, as in finish().
   __device__ __forceinline__ void run(int zb, int ze, bool down) {
     float cr[Q], cb[Q], nr[Q], nb[Q];
     float crr = 0.f, crb = 0.f, nrr = 0.f, nrb = 0.f;
-    int ccl = SOLID, ncl = SOLID;
+    int ccl = SOLID, ncl = SOLID, hcl = SOLID;
+    uint32_t hi = 0u, hhi = 0u;
     const int d = down ? -1 : 1;
     const int first = down ? ze - 1 : zb;
     const int n = ze - zb;
+    issue(first - d, ncl, hi, hcl, hhi);
     for (int o = 0; o < n + 2; ++o) {
       const int p = first + (o - 1) * d;
-      stage(p, o >= 1 && o <= n, nr, nb, nrr, nrb, ncl);
+      cp_async_wait_all();
+      take(p, o >= 1 && o <= n, ncl, hi, hcl, hhi, nr, nb, nrr, nrb);
+      const int pcl = ncl;
+      if (o + 1 < n + 2) issue(p + d, ncl, hi, hcl, hhi);
       __syncthreads();
       if (o >= 2) finish(p - d, cr, cb, crr, crb, ccl);
 #pragma unroll
       for (int i = 0; i < Q; ++i) { cr[i] = nr[i]; cb[i] = nb[i]; }
       crr = nrr;
       crb = nrb;
-      ccl = ncl;
+      ccl = pcl;
     }
   }
 

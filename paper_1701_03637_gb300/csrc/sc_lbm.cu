@@ -43,6 +43,7 @@ constexpr int kTileY[kNumTiles] = {8, 4, 8, 4};
 
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
+int wrap_host(int v, int n) { return ((v % n) + n) % n; }
 
 // ------------------------------------------------------------------ kernels
 
@@ -53,11 +54,12 @@ long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
 // a column's halo and shifted-pull sectors are read from DRAM once and then from
 // L2 by its neighbours. Chunks alternate their marching direction.
 template <int TX, int TY, class S>
-__global__ void __launch_bounds__(TX * TY, 2)
+__global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 1 ? 512 / (TX * TY) : 1)
     k_step(const LatDev L, const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
            double* __restrict__ evap_cum, int cols_x, int cols, int nch) {
   using TileT = Tile<TX, TY, S>;
-  __shared__ typename TileT::Smem sm;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  auto& sm = *reinterpret_cast<typename TileT::Smem*>(smem_raw);
   TileT t(L, sm, src, dst);
   const long long items = (long long)cols * nch;
   bool first = true;
@@ -324,17 +326,28 @@ struct StepArgs {
 };
 
 template <int TX, int TY, class S>
+constexpr size_t step_smem() { return sizeof(typename Tile<TX, TY, S>::Smem); }
+
+template <int TX, int TY, class S>
 cudaError_t launch_step(const StepArgs& a) {
-  k_step<TX, TY, S><<<a.G, TX * TY, 0, a.st>>>(a.L, (const typename S::T*)a.src, (typename S::T*)a.dst, a.evap,
-                                                a.cols_x, a.cols, a.nch);
+  k_step<TX, TY, S><<<a.G, TX * TY, step_smem<TX, TY, S>(), a.st>>>(
+      a.L, (const typename S::T*)a.src, (typename S::T*)a.dst, a.evap, a.cols_x, a.cols, a.nch);
   return cudaGetLastError();
 }
 
+// Resident CTAs per SM on the current device. Also opts the kernel in to its
+// dynamic shared memory there (above the 48 KB default); every handle calls this
+// on its device before its first step.
 template <int TX, int TY, class S>
 int occupancy_step() {
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step<TX, TY, S>, TX * TY, 0) != cudaSuccess) return 1;
-  return std::max(nb, 1);
+  if (cudaFuncSetAttribute(k_step<TX, TY, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)step_smem<TX, TY, S>()) != cudaSuccess)
+    return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step<TX, TY, S>, TX * TY, step_smem<TX, TY, S>()) !=
+      cudaSuccess)
+    return 0;
+  return nb;
 }
 
 using LaunchFn = cudaError_t (*)(const StepArgs&);
@@ -439,7 +452,7 @@ LatDev make_dev(const sc_params* p, const Layout& l) {
   L.rhoH_mass = 0.0;
   for (int i = 0; i < Q; ++i) L.rhoH_mass += (double)(wgt(i) * (float)p->rho_H);
   L.geometry = p->geometry;
-  L.sink_z0 = p->sink_z0; L.sink_layers = p->sink_layers;
+  L.sink_z0 = wrap_host(p->sink_z0, p->nz); L.sink_layers = p->sink_layers;
   L.scx = p->sphere_cx; L.scy = p->sphere_cy; L.scz = p->sphere_cz; L.RH2 = p->R_H * p->R_H;
   if (p->wall_thickness > 0) { L.wall_z0 = p->wall_z0; L.wall_z1 = p->wall_z0 + p->wall_thickness; }
   else { L.wall_z0 = 0; L.wall_z1 = 0; }
@@ -625,6 +638,10 @@ static int create_common(const sc_params* p, void* stream, void* buf, bool owns,
   // (ceil(items / G)) against the two extra planes each item stages; a caller
   // zchunk > 0 fixes the chunk length instead.
   const int occ = step_ops(p->storage, h->lay.tile).occupancy();
+  if (occ < 1) {
+    sc_lbm_destroy(h);
+    return fail(SC_ECUDA, "the step kernel cannot be made resident: %s", cudaGetErrorString(cudaGetLastError()));
+  }
   const long long slots = std::min<long long>((long long)sms * occ, h->lay.nslots);
   const long long cols = h->lay.cols;
   long long best_nch = 1;
