@@ -346,10 +346,141 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_ensemble(args):
+    """Batched ensemble of 64 lattices (edges log-uniform in [32, 96] per axis, films and
+    droplets, g and tau drawn per lattice) advanced by one persistent launch per step,
+    against the same lattices advanced one at a time through the single-lattice path."""
+    import numpy as np
+    import torch
+
+    import paper_1701_03637_gb300 as sc
+    from paper_1701_03637_gb300.workloads import ensemble
+
+    if int(os.environ.get("RANK", "0")) != 0:
+        return  # independent replicas only; the ensemble line is rank 0's
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    sc.build()
+    members = ensemble(64, 3, args.storage)
+    sizes = [p["nx"] * p["ny"] * p["nz"] for p, _ in members]
+    n = sum(sizes)
+    arena = sum(sc.required_bytes(p) + 256 for p, _ in members) + (1 << 20)
+    b = sc.Batch(arena, args.storage)
+    lats = []
+    for p, i in members:
+        _, lat = b.add(p)
+        lat.init(i)
+        lats.append(lat)
+    tile, zc = b.tune(trials=3)
+    stream = torch.cuda.current_stream()
+    b.step(args.warmup)
+    torch.cuda.synchronize()
+    sampler = ClockSampler()
+    time.sleep(0.3)
+    t0 = time.time()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t1 = time.time()
+    sampler.stop()
+    ms = e0.elapsed_time(e1)
+    bad = [k for k, lat in enumerate(lats) if lat.diagnostics()["status"] != 0]
+    value = n * args.steps / (ms * 1e-3) / 1e6
+    peak, peak_kind = measured_peak_hbm()
+    achieved = BYTES_PER_SITE[args.storage] * n / (ms * 1e-3 / args.steps) / 1e9
+
+    # the same lattices one at a time (fresh copies), each through its own fused launches
+    seq_steps = min(args.steps, 500)
+    singles = []
+    for p, i in members:
+        g = sc.Lattice(p)
+        g.init(i)
+        g.step(2)
+        singles.append(g)
+    torch.cuda.synchronize()
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    for g in singles:
+        g.step(seq_steps)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = s0.elapsed_time(s1)
+    seq_value = n * seq_steps / (seq_ms * 1e-3) / 1e6
+    for g in singles:
+        g.close()
+
+    # end to end: densities of every member from pinned host memory, the steps with
+    # every member's FP64 diagnostics read back every 100 steps, final densities to host
+    host_in = [(torch.from_numpy(np.ascontiguousarray(lat.read_fields()[0]).reshape(-1)).pin_memory(),
+                torch.from_numpy(np.ascontiguousarray(lat.read_fields()[1]).reshape(-1)).pin_memory()) for lat in lats]
+    host_out = [(torch.empty(lat.n, dtype=torch.float32).pin_memory(),
+                 torch.empty(lat.n, dtype=torch.float32).pin_memory()) for lat in lats]
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    for lat, (hr, hb) in zip(lats, host_in):
+        lat.init_fields_from(hr, hb)
+    done = ndiag = 0
+    while done < args.steps:
+        k = min(100, args.steps - done)
+        b.step(k)
+        done += k
+        for lat in lats:
+            lat.diagnostics()
+        ndiag += 1
+    for lat, (hr, hb) in zip(lats, host_out):
+        lat.read_fields_into(hr, hb)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - w0
+    diag_bytes = ndiag * sum(lat.diag_bytes() for lat in lats)
+    e2e = {"value": n * args.steps / wall / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": 8 * n / args.steps,
+           "d2h_bytes_per_step": (8 * n + diag_bytes) / args.steps,
+           "includes": "init of all 64 members from pinned host densities, all steps, every member's "
+                       "diagnostics every 100 steps, final densities to pinned host"}
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        cores = host_cores()
+        k = int(np.argmin(np.abs(np.asarray(sizes) - np.median(sizes))))
+        rate, steps = oracle_rate(members[k][0], members[k][1], 12.0, cores)
+        cpu = {"value": rate, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+               "sample": f"FP64 oracle on member {k} ({members[k][0]['nx']}x{members[k][0]['ny']}x"
+                         f"{members[k][0]['nz']}, the median size), {steps} steps"}
+    clk = sampler.summary(t0, t1)
+    info = b.info()
+    run_steps = 2000
+    out = {"metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
+           "config": {"workload": "ensemble_64: 64 two-component D3Q19 Shan-Chen lattices, edges "
+                                  "exp(U(ln 32, ln 96)) per axis, even = planar film on a wall, odd = droplet, "
+                                  "g ~ U(3.2, 3.8), tau ~ U(0.8, 1.2), master seed 3",
+                      "sites": n, "lattices_per_gpu": 64, "l2": "inputs larger than L2 (no flush)",
+                      "tile": sc.tile_list()[tile - 1], "zchunk": zc, "items": info["items"],
+                      "parallelism": "one persistent launch per step over all members"},
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                        "traffic": None, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                        "algorithmic_bytes_per_site": BYTES_PER_SITE[args.storage]},
+           "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps + (args.steps + 31) // 32,
+           "clocks": clk,
+           "one_at_a_time": {"value": seq_value, "unit": "MLUPS", "steps": seq_steps,
+                             "speedup_of_batch": value / seq_value},
+           "runs_per_hour": {"batched": 64 * 3600.0 / (ms * 1e-3 / args.steps * run_steps),
+                             "one_at_a_time": 64 * 3600.0 / (seq_ms * 1e-3 / seq_steps * run_steps),
+                             "run": f"{run_steps} steps per lattice"},
+           "members_with_bad_status": bad}
+    print(json.dumps(out))
+    b.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "ensemble_64":
+        run_ensemble(args)
     else:
         run_ours(args)
 

@@ -179,6 +179,56 @@ int sc_tile_list(int32_t* count, int32_t* tx_host, int32_t* ty_host, int32_t cap
 /* Thread-local message describing the last failure (never NULL). */
 const char* sc_last_error(void);
 
+/* ---------------------------------------------------------------- batched step
+   Many lattices (extents, tau, g, rho_H, geometry may all differ; the storage type
+   is the batch's) advanced together: one persistent launch per time step covers
+   every member, each member computing exactly what sc_lbm_step computes for it
+   (Sec. II), so a member's populations are bit-identical to the same lattice
+   stepped alone. The paper has no counterpart: this serves ensembles of runs. */
+typedef struct sc_batch sc_batch;
+
+/* A batch whose members live in one device arena of arena_bytes (cudaMalloc'd
+   here, freed by sc_batch_destroy). `stream` as for sc_lbm_create. */
+int sc_batch_create(size_t arena_bytes, int32_t storage, void* stream, sc_batch** out);
+/* Destroys every member and frees the arena. */
+void sc_batch_destroy(sc_batch* b);
+
+/* Admit a lattice: carve sc_lbm_required_bytes(p) from the arena (SC_ENOMEM when
+   no free range is large enough: admission by free device memory) and create it
+   there. *slot names it in this batch; *lattice (may be NULL) is a handle for
+   every sc_lbm_* call except sc_lbm_destroy and sc_lbm_set_stream: the batch owns
+   it (sc_lbm_destroy on it does nothing). The member starts with unlimited steps
+   and must be initialised (sc_lbm_init / _init_fields / _write_populations). */
+int sc_batch_add(sc_batch* b, const sc_params* p, int32_t* slot, sc_lbm** lattice);
+int sc_batch_lattice(sc_batch* b, int32_t slot, sc_lbm** lattice);
+/* Remove a member (synchronises the stream) and return its range to the arena. */
+int sc_batch_remove(sc_batch* b, int32_t slot);
+
+/* Steps the member still takes in sc_batch_step calls (< 0: unlimited); it stops
+   exactly after that many. sc_batch_remaining reads the count left. */
+int sc_batch_set_steps(sc_batch* b, int32_t slot, int64_t steps);
+int sc_batch_remaining(sc_batch* b, int32_t slot, int64_t* steps);
+
+/* Advance every member by min(nsteps, its remaining steps), asynchronously on the
+   batch's stream: a CUDA graph of 32 persistent launches plus the bookkeeping
+   kernel per 32 steps; CTAs claim (member, tile column, z chunk) items from a
+   per-launch counter. */
+int sc_batch_step(sc_batch* b, int64_t nsteps);
+
+/* Kernel configuration: tile (0 = automatic, k > 0 = entry k-1 of sc_tile_list)
+   and target planes per item (0 = 32). */
+int sc_batch_configure(sc_batch* b, int32_t tile, int32_t zchunk);
+/* Autotuner: time `trials` launches (<= 32) of every tile x {16, 32, 64}-plane
+   configuration on the current members, keep the fastest and report it. Trial
+   launches leave every member's state and bookkeeping unchanged (they write
+   only the buffer the next real step overwrites). Synchronous. */
+int sc_batch_tune(sc_batch* b, int32_t trials, int32_t* tile, int32_t* zchunk);
+/* Members, work items per launch, free arena bytes, largest free range, and the
+   configuration in use. Any output pointer may be NULL. */
+int sc_batch_info(sc_batch* b, int32_t* members, int64_t* items, size_t* free_bytes, size_t* largest_free,
+                  int32_t* tile, int32_t* zchunk);
+int sc_batch_sync(sc_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

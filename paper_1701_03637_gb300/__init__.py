@@ -18,7 +18,7 @@ Q = 19
 STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
 GEOMETRY = {"periodic": 0, "planar": 1, "sphere": 2}
 
-__all__ = ["Lattice", "ScError", "build", "lattice_directions", "tile_list", "required_bytes", "Q"]
+__all__ = ["Lattice", "Batch", "ScError", "build", "lattice_directions", "tile_list", "required_bytes", "Q"]
 
 _PARAM_DEFAULTS = dict(tau_r=1.0, tau_b=1.0, G=3.6, rho_H=0.03, geometry=0, sink_z0=0, sink_layers=1,
                        sphere_cx=0.0, sphere_cy=0.0, sphere_cz=0.0, R_H=0.0, wall_z0=0, wall_thickness=0,
@@ -102,10 +102,27 @@ class Lattice:
                                            C.c_void_p(aligned), C.c_size_t(nbytes), C.byref(h)))
         self._h = h
 
+    @classmethod
+    def _member(cls, handle, params: Params, device, stream, owner):
+        """A view of a lattice that a Batch owns (its memory is the batch's arena)."""
+        self = cls.__new__(cls)
+        import torch
+        self.torch = torch
+        self.device = device
+        self._p = params
+        self.params = {k: getattr(params, k) for k, _ in Params._fields_}
+        self.nx, self.ny, self.nz = params.nx, params.ny, params.nz
+        self.n = self.nx * self.ny * self.nz
+        self.shape = (self.nz, self.ny, self.nx)
+        self.stream = stream
+        self._owner = owner
+        self._h = handle
+        return self
+
     # ------------------------------------------------------------ lifecycle
     def close(self):
         h = getattr(self, "_h", None)
-        if h is not None and h.value:
+        if h is not None and h.value and getattr(self, "_owner", None) is None:
             _lib().sc_lbm_destroy(h)
         self._h = None
 
@@ -196,3 +213,87 @@ class Lattice:
         tx, ty, zc, n = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int64()
         check(_lib().sc_lbm_launch_info(self._h, C.byref(tx), C.byref(ty), C.byref(zc), C.byref(n)))
         return dict(tile_x=tx.value, tile_y=ty.value, zchunk=zc.value, ctas=n.value)
+
+
+class Batch:
+    """Many lattices advanced together by one persistent launch per time step.
+
+    Members live in a device arena of ``arena_bytes`` that the library allocates;
+    ``add`` fails with ``ScError`` (-2) when no free range fits the lattice, which
+    is the admission test of a serving loop. Each member is a ``Lattice`` view for
+    init, fields and diagnostics; ``step`` advances all members at once.
+    """
+
+    def __init__(self, arena_bytes: int, storage="f32", device=None, stream=None):
+        import torch
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
+        with torch.cuda.device(self.device):
+            self.stream = stream or torch.cuda.current_stream(self.device)
+            b = C.c_void_p()
+            check(_lib().sc_batch_create(C.c_size_t(int(arena_bytes)), self.storage,
+                                         C.c_void_p(self.stream.cuda_stream), C.byref(b)))
+        self._b = b
+        self._members = {}
+
+    def close(self):
+        b = getattr(self, "_b", None)
+        if b is not None and b.value:
+            for lat in self._members.values():
+                lat._h = None
+            self._members = {}
+            _lib().sc_batch_destroy(b)
+        self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add(self, params: dict):
+        """Admit a lattice; returns (slot, Lattice view)."""
+        p = make_params(dict(params, storage=self.storage))
+        slot, h = C.c_int32(), C.c_void_p()
+        check(_lib().sc_batch_add(self._b, C.byref(p), C.byref(slot), C.byref(h)))
+        lat = Lattice._member(h, p, self.device, self.stream, self)
+        self._members[slot.value] = lat
+        return slot.value, lat
+
+    def lattice(self, slot: int):
+        return self._members[slot]
+
+    def remove(self, slot: int) -> None:
+        check(_lib().sc_batch_remove(self._b, int(slot)))
+        lat = self._members.pop(slot, None)
+        if lat is not None:
+            lat._h = None
+
+    def set_steps(self, slot: int, steps: int) -> None:
+        check(_lib().sc_batch_set_steps(self._b, int(slot), int(steps)))
+
+    def remaining(self, slot: int) -> int:
+        v = C.c_int64()
+        check(_lib().sc_batch_remaining(self._b, int(slot), C.byref(v)))
+        return int(v.value)
+
+    def step(self, n: int = 1) -> None:
+        check(_lib().sc_batch_step(self._b, int(n)))
+
+    def configure(self, tile: int = 0, zchunk: int = 0) -> None:
+        check(_lib().sc_batch_configure(self._b, int(tile), int(zchunk)))
+
+    def tune(self, trials: int = 3):
+        t, z = C.c_int32(), C.c_int32()
+        check(_lib().sc_batch_tune(self._b, int(trials), C.byref(t), C.byref(z)))
+        return t.value, z.value
+
+    def info(self) -> dict:
+        m, it, fb, lf, t, z = C.c_int32(), C.c_int64(), C.c_size_t(), C.c_size_t(), C.c_int32(), C.c_int32()
+        check(_lib().sc_batch_info(self._b, C.byref(m), C.byref(it), C.byref(fb), C.byref(lf), C.byref(t),
+                                   C.byref(z)))
+        return dict(members=m.value, items=it.value, free_bytes=fb.value, largest_free=lf.value, tile=t.value,
+                    zchunk=z.value)
+
+    def sync(self) -> None:
+        check(_lib().sc_batch_sync(self._b))

@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(PKG, "_build")
 LIB_PATH = os.path.join(BUILD_DIR, "libsc_lbm.so")
 SOURCES = ["sc_lbm.cu"]
-HEADERS = ["sc_kernels.cuh"]
+HEADERS = ["sc_kernels.cuh", "sc_batch.cuh"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 _lock = threading.Lock()
@@ -106,6 +106,19 @@ _SIGS = {
     "sc_lbm_diagnostics_noalloc": (C.c_int, [_VP, _VP]),
     "sc_lbm_launch_info": (C.c_int, [_VP, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                      C.POINTER(C.c_int64)]),
+    "sc_batch_create": (C.c_int, [C.c_size_t, C.c_int32, _VP, C.POINTER(_VP)]),
+    "sc_batch_destroy": (None, [_VP]),
+    "sc_batch_add": (C.c_int, [_VP, C.POINTER(Params), C.POINTER(C.c_int32), C.POINTER(_VP)]),
+    "sc_batch_lattice": (C.c_int, [_VP, C.c_int32, C.POINTER(_VP)]),
+    "sc_batch_remove": (C.c_int, [_VP, C.c_int32]),
+    "sc_batch_set_steps": (C.c_int, [_VP, C.c_int32, C.c_int64]),
+    "sc_batch_remaining": (C.c_int, [_VP, C.c_int32, C.POINTER(C.c_int64)]),
+    "sc_batch_step": (C.c_int, [_VP, C.c_int64]),
+    "sc_batch_configure": (C.c_int, [_VP, C.c_int32, C.c_int32]),
+    "sc_batch_tune": (C.c_int, [_VP, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "sc_batch_info": (C.c_int, [_VP, C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_size_t),
+                                C.POINTER(C.c_size_t), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "sc_batch_sync": (C.c_int, [_VP]),
 }
 
 

@@ -478,6 +478,7 @@ struct sc_lbm {
   cudaGraphExec_t graph;
   int graph_len;
   int graph_cur;
+  sc_batch* owner;  // batch whose arena holds this lattice (it destroys the handle)
   void* pop(int k) const { return base + lay.off_pop[k]; }
   float* stage() const { return (float*)(base + lay.off_stage); }
   double* evap() const { return (double*)(base + lay.off_evap); }
@@ -696,7 +697,7 @@ int sc_lbm_create_ext(const sc_params* p, void* stream, void* buf, size_t bytes,
 }
 
 void sc_lbm_destroy(sc_lbm* h) {
-  if (!h) return;
+  if (!h || h->owner) return;  // a batch member goes with sc_batch_remove / sc_batch_destroy
   cudaStreamSynchronize(h->stream);
   if (h->graph) cudaGraphExecDestroy(h->graph);
   if (h->h_diag) cudaFreeHost(h->h_diag);
@@ -773,9 +774,12 @@ static int ensure_graph(sc_lbm* h) {
   return SC_OK;
 }
 
+static void batch_touch(sc_batch* b);  // the member's buffer parity changed outside the batch
+
 int sc_lbm_step(sc_lbm* h, int64_t nsteps) {
   if (!h) return fail(SC_EINVAL, "NULL handle");
   if (nsteps < 0) return fail(SC_EINVAL, "nsteps must be >= 0");
+  if (h->owner && nsteps > 0) batch_touch(h->owner);
   int64_t left = nsteps;
   if (left >= 4) {
     int rc = ensure_graph(h);
@@ -970,3 +974,5 @@ int sc_lbm_diag_bytes(sc_lbm* h, size_t* bytes) {
 }
 
 }  // extern "C"
+
+#include "sc_batch.cuh"

@@ -44,6 +44,63 @@ WORKLOADS = {
 }
 
 
+class SplitMix64:
+    """Counter stream of SplitMix64 (Steele, Lea and Flood 2014), for drawing
+    workload parameters; u() maps the top 53 bits to [0, 1)."""
+
+    M = (1 << 64) - 1
+
+    def __init__(self, seed: int):
+        self.x = seed & self.M
+
+    def next(self) -> int:
+        self.x = (self.x + 0x9E3779B97F4A7C15) & self.M
+        z = self.x
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & self.M
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & self.M
+        return z ^ (z >> 31)
+
+    def u(self) -> float:
+        return (self.next() >> 11) * 2.0 ** -53
+
+
+def ensemble_member(k: int, rng: "SplitMix64", lo: float = 32.0, hi: float = 96.0, cubic: bool = False,
+                    storage="f32"):
+    """One lattice of a randomised ensemble: edges exp(U(ln lo, ln hi)) (per axis, or one
+    for a cube), even k a planar film (wall z in {0, 1}, film below nz/4, sink plane
+    z = nz-1), odd k a floating droplet (radius U(0.2, 0.35) x the shortest edge, sinks
+    at the z-boundary planes); g ~ U(3.2, 3.8) and one tau ~ U(0.8, 1.2) for both
+    components; init seed from the stream."""
+    import math
+
+    def edge():
+        return int(round(math.exp(math.log(lo) + (math.log(hi) - math.log(lo)) * rng.u())))
+
+    if cubic:
+        nx = ny = nz = edge()
+    else:
+        nx, ny, nz = edge(), edge(), edge()
+    G = 3.2 + 0.6 * rng.u()
+    tau = 0.8 + 0.4 * rng.u()
+    seed = rng.next()
+    base = dict(nx=nx, ny=ny, nz=nz, tau_r=tau, tau_b=tau, G=G, rho_H=0.03, storage=storage)
+    if k % 2 == 0:
+        params = dict(base, geometry=1, sink_z0=nz - 1, sink_layers=1, wall_z0=0, wall_thickness=2)
+        init = dict(shape=0, film_z=max(3, nz // 4), rho_hi=1.0, rho_lo=0.03, noise_amp=1e-4, seed=seed)
+    else:
+        r = (0.2 + 0.15 * rng.u()) * min(nx, ny, nz)
+        params = dict(base, geometry=1, sink_z0=nz - 1, sink_layers=2)
+        init = dict(shape=1, cx=nx / 2.0, cy=ny / 2.0, cz=nz / 2.0, radius=r, rho_hi=1.0, rho_lo=0.03,
+                    noise_amp=1e-4, seed=seed)
+    return params, init
+
+
+def ensemble(count: int = 64, seed: int = 3, storage="f32"):
+    """A batched ensemble: count lattices drawn by ensemble_member from one stream."""
+    rng = SplitMix64(seed)
+    return [ensemble_member(k, rng, storage=storage) for k in range(count)]
+
+
 def random_populations(nx, ny, nz, seed, rho=(0.6, 0.1), spread=0.3):
     """Non-equilibrium populations f[c][i][z][y][x] = rho_c * U(1-spread, 1+spread) / 19,
     float64, seeded with numpy's PCG64."""
