@@ -127,7 +127,11 @@ def declared_symbols():
 
 
 class ScError(RuntimeError):
-    pass
+    """A library call failed; ``code`` is its SC_E* return value."""
+
+    def __init__(self, msg: str, code: int = 0):
+        super().__init__(msg)
+        self.code = code
 
 
 def load(path: str | None = None):
@@ -151,4 +155,4 @@ def load(path: str | None = None):
 def check(rc: int) -> None:
     if rc != 0:
         msg = load().sc_last_error().decode(errors="replace")
-        raise ScError(f"sc_lbm error {rc}: {msg}")
+        raise ScError(f"sc_lbm error {rc}: {msg}", rc)

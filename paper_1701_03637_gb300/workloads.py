@@ -122,3 +122,21 @@ def smooth_state(nx, ny, nz, seed, amp=0.05):
         rr += amp * np.cos(arg + ph[0])
         rb += amp * np.sin(arg + ph[1])
     return rr, rb
+
+
+def request_stream(count: int, rate: float, seed: int = 4, lo: float = 32.0, hi: float = 160.0,
+                   steps=(2000, 20000), storage="f16"):
+    """A served request stream: Poisson arrivals at `rate` per second (exponential gaps),
+    each request a cubic lattice (edge log-uniform in [lo, hi]) drawn like an ensemble
+    member, with a step count uniform in [steps[0], steps[1]]. Returns a list of
+    (arrival_s, params, init, nsteps)."""
+    import math
+    rng = SplitMix64(seed)
+    t = 0.0
+    out = []
+    for k in range(count):
+        t += -math.log(1.0 - rng.u()) / rate
+        params, init = ensemble_member(k, rng, lo, hi, cubic=True, storage=storage)
+        n = int(steps[0] + (steps[1] - steps[0]) * rng.u())
+        out.append((t, params, init, n))
+    return out
