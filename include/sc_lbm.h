@@ -60,6 +60,11 @@ extern "C" {
 #define SC_STORAGE_F16 1        /* FP16 offsets f_i - w_i*rho0 (rho0 = 1), FP32 arithmetic */
 #define SC_STORAGE_BF16 2       /* BF16 offsets f_i - w_i*rho0, FP32 arithmetic */
 
+#define SC_STAGING_AUTO 0       /* staged rows where nx allows, else per-thread pulls */
+#define SC_STAGING_THREAD 1     /* each thread copies its site's 38 pulls (any nx) */
+#define SC_STAGING_ROWS 2       /* the CTA copies the tile's source rows as 16-byte chunks
+                                   (nx a multiple of 4 for FP32, of 8 for FP16/BF16) */
+
 /* Physical and geometric parameters of one lattice (Sec. II; geometry of Sec. III). */
 typedef struct sc_params {
   int32_t nx, ny, nz;             /* lattice extent, each >= 1 */
@@ -73,6 +78,7 @@ typedef struct sc_params {
   int32_t storage;                /* SC_STORAGE_* */
   int32_t tile;                   /* kernel tile choice: 0 = automatic, k > 0 = entry k-1 of sc_tile_list */
   int32_t zchunk;                 /* planes per CTA along z: 0 = automatic */
+  int32_t staging;                /* SC_STAGING_*: how the step kernel gathers its pulls */
 } sc_params;
 
 /* Seeded initial state: film or droplet with uniform noise. */
@@ -169,8 +175,10 @@ int sc_lbm_profile(sc_lbm* h, double* phi_host);
    on a device share the array: calls whose work overlaps on the GPU race. */
 int sc_lbm_diagnostics_noalloc(sc_lbm* h, double* out_dev);
 
-/* Kernel configuration in use: tile extents, planes per CTA, grid size. */
-int sc_lbm_launch_info(sc_lbm* h, int32_t* tile_x, int32_t* tile_y, int32_t* zchunk, int64_t* ctas);
+/* Kernel configuration in use: tile extents, planes per CTA, grid size and the
+   staging (SC_STAGING_THREAD or SC_STAGING_ROWS). Any output pointer may be NULL. */
+int sc_lbm_launch_info(sc_lbm* h, int32_t* tile_x, int32_t* tile_y, int32_t* zchunk, int64_t* ctas,
+                       int32_t* staging);
 /* Bytes one sc_lbm_diagnostics / sc_lbm_profile call copies device-to-host. */
 int sc_lbm_diag_bytes(sc_lbm* h, size_t* bytes);
 /* Number of compiled tile shapes and their extents. */

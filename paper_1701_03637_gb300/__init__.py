@@ -22,7 +22,7 @@ __all__ = ["Lattice", "Batch", "ScError", "build", "lattice_directions", "tile_l
 
 _PARAM_DEFAULTS = dict(tau_r=1.0, tau_b=1.0, G=3.6, rho_H=0.03, geometry=0, sink_z0=0, sink_layers=1,
                        sphere_cx=0.0, sphere_cy=0.0, sphere_cz=0.0, R_H=0.0, wall_z0=0, wall_thickness=0,
-                       storage=0, tile=0, zchunk=0)
+                       storage=0, tile=0, zchunk=0, staging=0)
 _INIT_DEFAULTS = dict(shape=0, film_z=0, cx=0.0, cy=0.0, cz=0.0, radius=0.0, rho_hi=1.0, rho_lo=0.03,
                       noise_amp=0.0, seed=0)
 
@@ -210,9 +210,10 @@ class Lattice:
         return int(b.value)
 
     def launch_info(self) -> dict:
-        tx, ty, zc, n = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int64()
-        check(_lib().sc_lbm_launch_info(self._h, C.byref(tx), C.byref(ty), C.byref(zc), C.byref(n)))
-        return dict(tile_x=tx.value, tile_y=ty.value, zchunk=zc.value, ctas=n.value)
+        tx, ty, zc, n, st = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int64(), C.c_int32()
+        check(_lib().sc_lbm_launch_info(self._h, C.byref(tx), C.byref(ty), C.byref(zc), C.byref(n), C.byref(st)))
+        return dict(tile_x=tx.value, tile_y=ty.value, zchunk=zc.value, ctas=n.value,
+                    staging={1: "thread", 2: "rows"}.get(st.value, st.value))
 
 
 class Batch:

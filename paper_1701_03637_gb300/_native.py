@@ -63,7 +63,8 @@ class Params(C.Structure):
                 ("geometry", C.c_int32), ("sink_z0", C.c_int32), ("sink_layers", C.c_int32),
                 ("sphere_cx", C.c_double), ("sphere_cy", C.c_double), ("sphere_cz", C.c_double),
                 ("R_H", C.c_double), ("wall_z0", C.c_int32), ("wall_thickness", C.c_int32),
-                ("storage", C.c_int32), ("tile", C.c_int32), ("zchunk", C.c_int32)]
+                ("storage", C.c_int32), ("tile", C.c_int32), ("zchunk", C.c_int32),
+                ("staging", C.c_int32)]
 
 
 class Init(C.Structure):
@@ -105,7 +106,7 @@ _SIGS = {
     "sc_lbm_diag_bytes": (C.c_int, [_VP, C.POINTER(C.c_size_t)]),
     "sc_lbm_diagnostics_noalloc": (C.c_int, [_VP, _VP]),
     "sc_lbm_launch_info": (C.c_int, [_VP, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
-                                     C.POINTER(C.c_int64)]),
+                                     C.POINTER(C.c_int64), C.POINTER(C.c_int32)]),
     "sc_batch_create": (C.c_int, [C.c_size_t, C.c_int32, _VP, C.POINTER(_VP)]),
     "sc_batch_destroy": (None, [_VP]),
     "sc_batch_add": (C.c_int, [_VP, C.POINTER(Params), C.POINTER(C.c_int32), C.POINTER(_VP)]),

@@ -72,6 +72,12 @@ __device__ __forceinline__ void cp_async4(uint32_t* smem, const void* gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
+// 16-byte asynchronous copy kept in L2 only (each row is read once per CTA).
+// Both addresses must be 16-byte aligned.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
@@ -213,28 +219,29 @@ __device__ __forceinline__ uint32_t pull_async(const LatDev& L, const typename S
   return hi;
 }
 
-// Same loads, summed in the same order as sum19() so both give identical bits.
-template <class S>
-__device__ __forceinline__ void pull_sums(const LatDev& L, const typename S::T* __restrict__ src, const PullIdx& P,
-                                          float& rr, float& rb) {
-  const long long cstride = (long long)Q * L.np;
-  rr = 0.0f;
-  rb = 0.0f;
-  Unroll<0, Q>::run([&](auto ic) {
-    constexpr int I = decltype(ic)::value;
-    int idx, d;
-    P.template at<I>(idx, d);
-    const typename S::T* p = src + (long long)d * L.np + idx;
-    rr = rr + S::ld(p, wgt(I));
-    rb = rb + S::ld(p + cstride, wgt(I));
-  });
+// Density from the 19 populations of a site, summed pairwise (depth 5, so the
+// additions overlap) in one fixed order that every kernel uses; get(i) yields
+// population i, so values can be summed as they are loaded.
+template <class Get>
+__device__ __forceinline__ float sum19_of(Get&& get) {
+  const float a0 = __fadd_rn(get(std::integral_constant<int, 0>()), get(std::integral_constant<int, 1>()));
+  const float a1 = __fadd_rn(get(std::integral_constant<int, 2>()), get(std::integral_constant<int, 3>()));
+  const float b0 = __fadd_rn(a0, a1);
+  const float a2 = __fadd_rn(get(std::integral_constant<int, 4>()), get(std::integral_constant<int, 5>()));
+  const float a3 = __fadd_rn(get(std::integral_constant<int, 6>()), get(std::integral_constant<int, 7>()));
+  const float b1 = __fadd_rn(a2, a3);
+  const float a4 = __fadd_rn(get(std::integral_constant<int, 8>()), get(std::integral_constant<int, 9>()));
+  const float a5 = __fadd_rn(get(std::integral_constant<int, 10>()), get(std::integral_constant<int, 11>()));
+  const float b2 = __fadd_rn(a4, a5);
+  const float a6 = __fadd_rn(get(std::integral_constant<int, 12>()), get(std::integral_constant<int, 13>()));
+  const float a7 = __fadd_rn(get(std::integral_constant<int, 14>()), get(std::integral_constant<int, 15>()));
+  const float b3 = __fadd_rn(a6, a7);
+  const float a8 = __fadd_rn(get(std::integral_constant<int, 16>()), get(std::integral_constant<int, 17>()));
+  const float b4 = __fadd_rn(a8, get(std::integral_constant<int, 18>()));
+  return __fadd_rn(__fadd_rn(__fadd_rn(b0, b1), __fadd_rn(b2, b3)), b4);
 }
-
 __device__ __forceinline__ float sum19(const float (&f)[Q]) {
-  float r = 0.0f;
-#pragma unroll
-  for (int i = 0; i < Q; ++i) r = r + f[i];
-  return r;
+  return sum19_of([&](auto ic) { return f[decltype(ic)::value]; });
 }
 
 // Evaporation boundary (Sec. II C) on the densities of the arrived populations:
@@ -487,14 +494,15 @@ struct Tile {
       float hpr = 0.0f, hpb = 0.0f;
       if (hcl != SOLID) {
         const uint32_t* w = halo_slot();
-        // summed in sum19's order, so the halo Psi has the owner's bits
-        float hrr = 0.0f, hrb = 0.0f;
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-          const uint32_t h = (hhi >> i) & 1u;
-          hrr = hrr + S::word(w[i * HS], h, wgt(i));
-          hrb = hrb + S::word(w[(Q + i) * HS], h, wgt(i));
-        }
+        // the owner's arithmetic, so the halo Psi has the owner's bits
+        float hrr = sum19_of([&](auto ic) {
+          constexpr int I = decltype(ic)::value;
+          return S::word(w[I * HS], (hhi >> I) & 1u, wgt(I));
+        });
+        float hrb = sum19_of([&](auto ic) {
+          constexpr int I = decltype(ic)::value;
+          return S::word(w[(Q + I) * HS], (hhi >> I) & 1u, wgt(I));
+        });
         if (hcl == SINK) sink_densities(L, hrr, hrb);
         hpr = psi_of(hrr);
         hpb = psi_of(hrb);
@@ -554,6 +562,233 @@ struct Tile {
   }
 
   // Block sum of the evaporated mass (fixed order: warps, then warp 0's lanes).
+  __device__ __forceinline__ double block_evap() {
+    double v = evap;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sm.red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+      for (int k = 0; k < NT / 32; ++k) t += sm.red[k];
+    return t;
+  }
+};
+
+// ------------------------------------------------------------------ fused step, staged rows
+//
+// The same march as Tile, with the pulls staged cooperatively. For each of the
+// 38 (component, direction) pairs the plane's source rows -- the TY + 2 rows
+// y0 - 1 .. y0 + TY shifted by -e_y, in plane z - e_z -- are copied into shared
+// memory over columns x0 - E .. x0 + TX + E as aligned 16-byte chunks (E
+// populations each), and the x shift -e_x is applied when a thread reads them.
+// The E-column margins hold the side halo, so the halo needs no pulls of its
+// own. Chunks are spread evenly over the CTA's threads (a per-plane table holds
+// each row's offset, a per-column table each chunk's wrapped x), so no warp
+// carries more copy work than another. Requires nx % E == 0 (then every
+// wrapped chunk is aligned). A population whose source plane is solid is the
+// site's own opposite population (halfway bounce-back): read directly.
+//
+// Per plane: wait for the copies, barrier, read out plane p (Psi to the ring,
+// own populations to registers), write the row table of plane p + d, barrier,
+// start plane p + d's copies, collide plane p - d.
+template <int TX, int TY, class S>
+struct TileRows {
+  using T = typename S::T;
+  static constexpr int E = 16 / (int)sizeof(T);           // populations per chunk
+  static constexpr int NT = TX * TY, NW = NT / 32, RW = TX + 2, RH = TY + 2, NH = 2 * TX + 2 * RH;
+  static constexpr int SW = TX + 2 * E;                   // staged row width
+  static constexpr int CH = SW / E;                       // chunks per row
+  static constexpr int NR = 2 * Q * RH;                   // staged rows per plane
+  static constexpr int RS = NT / CH;                      // rows copied per pass of the CTA
+  static_assert(TX % E == 0, "tile width must be a multiple of the chunk");
+  static_assert(NH <= NT && NT % 32 == 0, "tile shape");
+
+  struct Smem {
+    T stage[2 * Q][RH][SW];  // rows of plane p: [c Q + i][y - y0 + 1][x - x0 + E]
+    float ring[2][4][RH][RW];
+    const T* rowp[NR];       // source address of each staged row's column x = 0
+    int chx[CH];             // wrapped x of chunk j
+    double red[NW];
+  };
+
+  const LatDev& L;
+  Smem& sm;
+  const T* __restrict__ src;
+  T* __restrict__ dst;
+  int tx, ty, x, y, hx, hy, hlx, hly, y0;
+  int cr0, cj;  // this thread's copy work: rows cr0, cr0 + RS, ... at chunk cj (cr0 >= NR: none)
+  bool active, has_halo;
+  double evap;
+
+  __device__ __forceinline__ TileRows(const LatDev& L_, Smem& sm_, const T* s_, T* d_)
+      : L(L_), sm(sm_), src(s_), dst(d_), evap(0.0) {}
+
+  __device__ __forceinline__ int wrapz(int z) const { return z < 0 ? z + L.nz : (z >= L.nz ? z - L.nz : z); }
+
+  __device__ __forceinline__ void setup(int bx, int by) {
+    const int tid = threadIdx.x;
+    tx = tid % TX;
+    ty = tid / TX;
+    const int gx = bx * TX + tx, gy = by * TY + ty;
+    active = gx < L.nx && gy < L.ny;
+    x = gx % L.nx;
+    y = gy % L.ny;
+    y0 = by * TY;
+    const int h = tid;  // halo slot: top row, bottom row, left column, right column
+    has_halo = h < NH;
+    if (h < TX) { hlx = h; hly = -1; }
+    else if (h < 2 * TX) { hlx = h - TX; hly = TY; }
+    else if (h < 2 * TX + RH) { hlx = -1; hly = h - 2 * TX - 1; }
+    else { hlx = TX; hly = h - 2 * TX - RH - 1; }
+    hx = wrapi(bx * TX + hlx, L.nx);
+    hy = wrapi(by * TY + hly, L.ny);
+    if (tid < CH) sm.chx[tid] = wrapi(bx * TX - E + tid * E, L.nx);
+    cj = tid % CH;
+    cr0 = tid < RS * CH ? tid / CH : NR;
+  }
+
+  // Row table of plane p (p in [-1, nz]).
+  __device__ __forceinline__ void table(int p) {
+    const int zp = wrapz(p);
+    for (int R = threadIdx.x; R < NR; R += NT) {
+      const int ci = R / RH, r = R - ci * RH, i = ci % Q;
+      const int zs = wrapz(zp - dir_z(i)), ys = wrapi(y0 - 1 + r - dir_y(i), L.ny);
+      sm.rowp[R] = src + ((long long)ci * L.np + (long long)zs * L.nxny + (long long)ys * L.nx);
+    }
+  }
+
+  // Copies of the plane whose table is current: this thread's chunk column cj of
+  // rows cr0, cr0 + RS, ...; cx is that column's wrapped x.
+  __device__ __forceinline__ void issue(int cx) {
+    T* to = &sm.stage[0][0][0] + cr0 * SW + cj * E;
+#pragma unroll 4
+    for (int R = cr0; R < NR; R += RS, to += RS * SW) cp_async16(to, sm.rowp[R] + cx);
+    cp_async_commit();
+  }
+
+  // Population i of component c arriving at tile cell (lx, ly) (ly, lx in [-1, TY] x [-1, TX]):
+  // from the staged rows; next to a wall, a population whose source plane is solid
+  // is the site's (index s) own opposite one instead.
+  template <int I>
+  __device__ __forceinline__ float staged(int c, int ly, int lx) const {
+    return S::cv(sm.stage[c * Q + I][ly + 1][lx + E - dir_x(I)], wgt(I));
+  }
+  template <int I>
+  __device__ __forceinline__ float pulled(int c, int ly, int lx, bool sol_m, bool sol_p, uint32_t s) const {
+    constexpr int ez = dir_z(I);
+    if (ez != 0 && (ez > 0 ? sol_m : sol_p))
+      return S::ld(src + (long long)(c * Q + opp(I)) * L.np + s, wgt(I));
+    return staged<I>(c, ly, lx);
+  }
+
+  // Read plane p out of the staged rows: the own site into fr/fb, the halo site
+  // as sums (the owner's arithmetic, so the halo Psi has the owner's bits); apply the
+  // sink and publish Psi to ring slot p & 3. Returns the own site's class.
+  __device__ __forceinline__ int take(int p, bool own, float (&fr)[Q], float (&fb)[Q], float& rr, float& rb) {
+    const int zp = wrapz(p), slot = p & 3;
+    const bool sol_m = solid_z(L, zp == 0 ? L.nz - 1 : zp - 1), sol_p = solid_z(L, zp == L.nz - 1 ? 0 : zp + 1);
+    const int cls = site_class(L, x, y, zp);
+    float pr = 0.0f, pb = 0.0f;
+    const bool walls = sol_m || sol_p;  // the same for the whole plane
+    if (cls == SOLID) {
+      rr = rb = 0.0f;
+    } else {
+      if (!walls) {
+        Unroll<0, Q>::run([&](auto ic) {
+          constexpr int I = decltype(ic)::value;
+          fr[I] = staged<I>(0, ty, tx);
+          fb[I] = staged<I>(1, ty, tx);
+        });
+      } else {
+        const uint32_t s = (uint32_t)(x + L.nx * y) + (uint32_t)L.nxny * (uint32_t)zp;
+        Unroll<0, Q>::run([&](auto ic) {
+          constexpr int I = decltype(ic)::value;
+          fr[I] = pulled<I>(0, ty, tx, sol_m, sol_p, s);
+          fb[I] = pulled<I>(1, ty, tx, sol_m, sol_p, s);
+        });
+      }
+      rr = sum19(fr);
+      rb = sum19(fb);
+      if (cls == SINK) {
+        if (active && own) evap += (double)sink_excess(L, fr);
+        sink_densities(L, rr, rb);
+      }
+      pr = psi_of(rr);
+      pb = psi_of(rb);
+    }
+    sm.ring[0][slot][ty + 1][tx + 1] = pr;
+    sm.ring[1][slot][ty + 1][tx + 1] = pb;
+    if (has_halo) {
+      const int hcl = site_class(L, hx, hy, zp);
+      float hpr = 0.0f, hpb = 0.0f;
+      if (hcl != SOLID) {
+        // the owner's arithmetic, so the halo Psi has the owner's bits
+        float hrr, hrb;
+        if (!walls) {
+          hrr = sum19_of([&](auto ic) { return staged<decltype(ic)::value>(0, hly, hlx); });
+          hrb = sum19_of([&](auto ic) { return staged<decltype(ic)::value>(1, hly, hlx); });
+        } else {
+          const uint32_t s = (uint32_t)(hx + L.nx * hy) + (uint32_t)L.nxny * (uint32_t)zp;
+          hrr = sum19_of([&](auto ic) { return pulled<decltype(ic)::value>(0, hly, hlx, sol_m, sol_p, s); });
+          hrb = sum19_of([&](auto ic) { return pulled<decltype(ic)::value>(1, hly, hlx, sol_m, sol_p, s); });
+        }
+        if (hcl == SINK) sink_densities(L, hrr, hrb);
+        hpr = psi_of(hrr);
+        hpb = psi_of(hrb);
+      }
+      sm.ring[0][slot][hly + 1][hlx + 1] = hpr;
+      sm.ring[1][slot][hly + 1][hlx + 1] = hpb;
+    }
+    return cls;
+  }
+
+  // Collide plane z (in [0, nz); read out one plane earlier) and store f*.
+  __device__ __forceinline__ void finish(int z, float (&fr)[Q], float (&fb)[Q], float rr, float rb, int cls) {
+    if (!active || cls == SOLID) return;
+    const int s = x + L.nx * y + L.nxny * z;
+    if (cls == SINK) {
+#pragma unroll
+      for (int i = 0; i < Q; ++i) { fr[i] = rest_pop(i, rr); fb[i] = rest_pop(i, rb); }
+    } else {
+      float ar[3], ab[3];
+      auto psi = [&](int c, int sl, int ly, int lx) { return sm.ring[c][sl][ly + 1][lx + 1]; };
+      force_sums(psi, (z - 1) & 3, z & 3, (z + 1) & 3, ty, tx, ar, ab);
+      const float psr = sm.ring[0][z & 3][ty + 1][tx + 1], psb = sm.ring[1][z & 3][ty + 1][tx + 1];
+      collide(L, fr, fb, rr, rb, psr, psb, ar, ab);
+    }
+    store_site<S>(L, dst, s, fr, fb);
+  }
+
+  __device__ __forceinline__ void run(int zb, int ze, bool down) {
+    float cr[Q], cb[Q], nr[Q], nb[Q];
+    float crr = 0.f, crb = 0.f, nrr = 0.f, nrb = 0.f;
+    int ccl = SOLID;
+    const int d = down ? -1 : 1;
+    const int first = down ? ze - 1 : zb;
+    const int n = ze - zb;
+    table(first - d);
+    __syncthreads();  // chunk and row tables
+    const int cx = sm.chx[cj];
+    issue(cx);
+    for (int o = 0; o < n + 2; ++o) {
+      const int p = first + (o - 1) * d;
+      cp_async_wait_all();
+      __syncthreads();  // every thread's copies of plane p have landed
+      const int pcl = take(p, o >= 1 && o <= n, nr, nb, nrr, nrb);
+      if (o + 1 < n + 2) table(p + d);
+      __syncthreads();  // ring complete, staged rows read out, next table written
+      if (o + 1 < n + 2) issue(cx);
+      if (o >= 2) finish(p - d, cr, cb, crr, crb, ccl);
+#pragma unroll
+      for (int i = 0; i < Q; ++i) { cr[i] = nr[i]; cb[i] = nb[i]; }
+      crr = nrr;
+      crb = nrb;
+      ccl = pcl;
+    }
+  }
+
   __device__ __forceinline__ double block_evap() {
     double v = evap;
 #pragma unroll

@@ -47,17 +47,18 @@ int wrap_host(int v, int n) { return ((v % n) + n) % n; }
 
 // ------------------------------------------------------------------ kernels
 
-// Persistent fused step (per-thread loads). The lattice is cut into tile columns
+// Persistent fused step; Rows selects the staged-rows marcher (TileRows) over
+// the per-thread one (Tile). The lattice is cut into tile columns
 // of TX x TY sites and z into nch chunks; item i = (chunk i / cols, column
 // i % cols). CTA b takes items b, b + G, b + 2G, ... so in every round the G
 // resident CTAs work on neighbouring columns of the same chunk in lock-step, and
 // a column's halo and shifted-pull sectors are read from DRAM once and then from
 // L2 by its neighbours. Chunks alternate their marching direction.
-template <int TX, int TY, class S>
+template <int TX, int TY, class S, bool Rows>
 __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 1 ? 512 / (TX * TY) : 1)
     k_step(const LatDev L, const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
            double* __restrict__ evap_cum, int cols_x, int cols, int nch) {
-  using TileT = Tile<TX, TY, S>;
+  using TileT = std::conditional_t<Rows, TileRows<TX, TY, S>, Tile<TX, TY, S>>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   auto& sm = *reinterpret_cast<typename TileT::Smem*>(smem_raw);
   TileT t(L, sm, src, dst);
@@ -325,12 +326,14 @@ struct StepArgs {
   cudaStream_t st;
 };
 
-template <int TX, int TY, class S>
-constexpr size_t step_smem() { return sizeof(typename Tile<TX, TY, S>::Smem); }
+template <int TX, int TY, class S, bool Rows = false>
+constexpr size_t step_smem() {
+  return Rows ? sizeof(typename TileRows<TX, TY, S>::Smem) : sizeof(typename Tile<TX, TY, S>::Smem);
+}
 
-template <int TX, int TY, class S>
+template <int TX, int TY, class S, bool Rows>
 cudaError_t launch_step(const StepArgs& a) {
-  k_step<TX, TY, S><<<a.G, TX * TY, step_smem<TX, TY, S>(), a.st>>>(
+  k_step<TX, TY, S, Rows><<<a.G, TX * TY, step_smem<TX, TY, S, Rows>(), a.st>>>(
       a.L, (const typename S::T*)a.src, (typename S::T*)a.dst, a.evap, a.cols_x, a.cols, a.nch);
   return cudaGetLastError();
 }
@@ -338,14 +341,14 @@ cudaError_t launch_step(const StepArgs& a) {
 // Resident CTAs per SM on the current device. Also opts the kernel in to its
 // dynamic shared memory there (above the 48 KB default); every handle calls this
 // on its device before its first step.
-template <int TX, int TY, class S>
+template <int TX, int TY, class S, bool Rows>
 int occupancy_step() {
   int nb = 0;
-  if (cudaFuncSetAttribute(k_step<TX, TY, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)step_smem<TX, TY, S>()) != cudaSuccess)
+  if (cudaFuncSetAttribute(k_step<TX, TY, S, Rows>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)step_smem<TX, TY, S, Rows>()) != cudaSuccess)
     return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step<TX, TY, S>, TX * TY, step_smem<TX, TY, S>()) !=
-      cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step<TX, TY, S, Rows>, TX * TY,
+                                                    step_smem<TX, TY, S, Rows>()) != cudaSuccess)
     return 0;
   return nb;
 }
@@ -356,21 +359,21 @@ struct StepOps {
   int (*occupancy)();  // resident CTAs per SM
 };
 
-template <class S>
+template <class S, bool Rows>
 StepOps pick_step(int tile) {
   switch (tile) {
-    case 0: return {&launch_step<32, 8, S>, &occupancy_step<32, 8, S>};
-    case 1: return {&launch_step<32, 4, S>, &occupancy_step<32, 4, S>};
-    case 2: return {&launch_step<16, 8, S>, &occupancy_step<16, 8, S>};
-    default: return {&launch_step<8, 4, S>, &occupancy_step<8, 4, S>};
+    case 0: return {&launch_step<32, 8, S, Rows>, &occupancy_step<32, 8, S, Rows>};
+    case 1: return {&launch_step<32, 4, S, Rows>, &occupancy_step<32, 4, S, Rows>};
+    case 2: return {&launch_step<16, 8, S, Rows>, &occupancy_step<16, 8, S, Rows>};
+    default: return {&launch_step<8, 4, S, Rows>, &occupancy_step<8, 4, S, Rows>};
   }
 }
 
-StepOps step_ops(int storage, int tile) {
+StepOps step_ops(int storage, int tile, bool rows) {
   switch (storage) {
-    case SC_STORAGE_F16: return pick_step<StF16>(tile);
-    case SC_STORAGE_BF16: return pick_step<StBF16>(tile);
-    default: return pick_step<StF32>(tile);
+    case SC_STORAGE_F16: return rows ? pick_step<StF16, true>(tile) : pick_step<StF16, false>(tile);
+    case SC_STORAGE_BF16: return rows ? pick_step<StBF16, true>(tile) : pick_step<StBF16, false>(tile);
+    default: return rows ? pick_step<StF32, true>(tile) : pick_step<StF32, false>(tile);
   }
 }
 
@@ -380,6 +383,7 @@ size_t elem_size(int storage) { return storage == SC_STORAGE_F32 ? 4 : 2; }
 
 struct Layout {
   int tile, tx, ty, cols_x, cols;
+  bool rows;                  // staged-rows step kernel (nx a multiple of a 16-byte chunk)
   long long np;               // array stride (elements)
   long long nsites, stage_n;  // sites; staging floats per component
   long long units, nslots;
@@ -399,6 +403,7 @@ Layout make_layout(const sc_params* p) {
   l.tile = p->tile > 0 ? p->tile - 1 : auto_tile(p);
   l.tx = kTileX[l.tile];
   l.ty = kTileY[l.tile];
+  l.rows = p->staging == SC_STAGING_ROWS || (p->staging == SC_STAGING_AUTO && p->nx % (16 / es) == 0);
   l.nsites = (long long)p->nx * p->ny * p->nz;
   l.np = round_up(l.nsites, 128 / es);  // each array starts 128-byte aligned
   l.stage_n = round_up(l.nsites, 64);
@@ -434,6 +439,9 @@ int validate(const sc_params* p) {
   if (p->storage < 0 || p->storage > 2) return fail(SC_EINVAL, "unknown storage %d", p->storage);
   if (p->tile < 0 || p->tile > kNumTiles) return fail(SC_EINVAL, "tile index out of range");
   if (p->zchunk < 0) return fail(SC_EINVAL, "zchunk must be >= 0");
+  if (p->staging < SC_STAGING_AUTO || p->staging > SC_STAGING_ROWS) return fail(SC_EINVAL, "unknown staging %d", p->staging);
+  if (p->staging == SC_STAGING_ROWS && p->nx % (p->storage == SC_STORAGE_F32 ? 4 : 8) != 0)
+    return fail(SC_EINVAL, "staged rows need nx to be a multiple of %d", p->storage == SC_STORAGE_F32 ? 4 : 8);
   if ((long long)p->nx > (1 << 20) || (long long)p->ny > (1 << 20) || (long long)p->nz > (1 << 20))
     return fail(SC_EINVAL, "lattice extent too large");
   if ((long long)p->nx * p->ny * p->nz > (1LL << 31) - 4096)
@@ -490,7 +498,7 @@ namespace {
 int launch_one(sc_lbm* h, cudaStream_t st) {
   const int src = h->cur, dst = 1 - h->cur;
   StepArgs a{h->L, h->pop(src), h->pop(dst), h->evap(), h->lay.cols_x, h->lay.cols, h->nch, h->grid, st};
-  cudaError_t e = step_ops(h->p.storage, h->lay.tile).launch(a);
+  cudaError_t e = step_ops(h->p.storage, h->lay.tile, h->lay.rows).launch(a);
   if (e != cudaSuccess) return fail(SC_ECUDA, "step launch failed: %s", cudaGetErrorString(e));
   h->cur = dst;
   return SC_OK;
@@ -638,7 +646,7 @@ static int create_common(const sc_params* p, void* stream, void* buf, bool owns,
   // Persistent grid of every resident CTA slot. The z chunk count trades rounds
   // (ceil(items / G)) against the two extra planes each item stages; a caller
   // zchunk > 0 fixes the chunk length instead.
-  const int occ = step_ops(p->storage, h->lay.tile).occupancy();
+  const int occ = step_ops(p->storage, h->lay.tile, h->lay.rows).occupancy();
   if (occ < 1) {
     sc_lbm_destroy(h);
     return fail(SC_ECUDA, "the step kernel cannot be made resident: %s", cudaGetErrorString(cudaGetLastError()));
@@ -958,8 +966,9 @@ int sc_lbm_diagnostics_noalloc(sc_lbm* h, double* out_dev) {
   return SC_OK;
 }
 
-int sc_lbm_launch_info(sc_lbm* h, int32_t* tx, int32_t* ty, int32_t* zchunk, int64_t* ctas) {
+int sc_lbm_launch_info(sc_lbm* h, int32_t* tx, int32_t* ty, int32_t* zchunk, int64_t* ctas, int32_t* staging) {
   if (!h) return fail(SC_EINVAL, "NULL handle");
+  if (staging) *staging = h->lay.rows ? SC_STAGING_ROWS : SC_STAGING_THREAD;
   if (tx) *tx = h->lay.tx;
   if (ty) *ty = h->lay.ty;
   if (zchunk) *zchunk = (int32_t)((h->p.nz + h->nch - 1) / h->nch);

@@ -51,7 +51,9 @@ GEOMS = {
     "sphere_sink": dict(geometry=2, sphere_cx=10.0, sphere_cy=5.5, sphere_cz=4.0, R_H=4.5, rho_H=0.025),
     "unequal_tau": dict(tau_r=0.8, tau_b=1.3, G=2.5),
 }
-SHAPES = [(37, 13, 11), (5, 3, 4), (1, 6, 9), (70, 9, 8), (33, 17, 5)]
+# nx not a multiple of 4: per-thread pulls; nx a multiple of 8: staged rows (FP32 and FP16/BF16)
+SHAPES = [(37, 13, 11), (5, 3, 4), (1, 6, 9), (70, 9, 8), (33, 17, 5),
+          (40, 13, 11), (8, 3, 4), (4, 6, 9), (72, 9, 8), (24, 17, 5)]
 
 
 # step kernel tiles: 0 = automatic choice, k > 0 = entry k - 1 of the tile list (32x8, 32x4, 16x8, 8x4)
@@ -160,15 +162,25 @@ def test_droplet_48_500_steps(sc, oracle_mod, kernel):
     _check_bookkeeping(dg, do, 500)
 
 
-def test_tiles_and_chunks_give_identical_bits(sc):
-    """The per-site arithmetic does not depend on the tile shape, z-chunking or graph replay."""
+@pytest.mark.parametrize("nx,stagings", [(41, (0,)), (40, (1, 2)), (8, (1, 2))])
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_tiles_and_chunks_give_identical_bits(sc, nx, stagings, storage):
+    """The per-site arithmetic does not depend on the tile shape, z-chunking, the
+    staging of the pulls or graph replay (a wall and a spherical sink included)."""
     from paper_1701_03637_gb300.workloads import droplet
     params, init = droplet(40, 9.0, 3, spherical_sink=True)
-    params.update(nx=41, ny=23, nz=19, sphere_cx=20.0, sphere_cy=11.0, sphere_cz=9.0, R_H=9.0)
-    init.update(cx=20.0, cy=11.0, cz=9.0, radius=6.0)
+    params.update(nx=nx, ny=23, nz=19, sphere_cx=nx / 2.0, sphere_cy=11.0, sphere_cz=9.0, R_H=9.0,
+                  wall_z0=0, wall_thickness=2, storage=storage)
+    init.update(cx=nx / 2.0, cy=11.0, cz=9.0, radius=min(6.0, nx / 2.0 - 1))
+    if storage == "f16" and nx % 8:
+        stagings = (0,)
     ref = None
-    for k, (tile, zc) in enumerate([(1, 0), (2, 3), (3, 1), (4, 19), (1, 5), (2, 0), (3, 7)]):
-        g = sc.Lattice(dict(params, tile=tile, zchunk=zc))
+    launches = [(st, tile, zc) for st in stagings
+                for tile, zc in [(1, 0), (2, 3), (3, 1), (4, 19), (1, 5), (2, 0), (3, 7)]]
+    for k, (st, tile, zc) in enumerate(launches):
+        g = sc.Lattice(dict(params, tile=tile, zchunk=zc, staging=st))
+        if st:
+            assert g.launch_info()["staging"] == {1: "thread", 2: "rows"}[st]
         g.init(init)
         if k == 4:
             for _ in range(30):
@@ -179,7 +191,7 @@ def test_tiles_and_chunks_give_identical_bits(sc):
         if ref is None:
             ref = f
         else:
-            assert np.array_equal(f, ref), (tile, zc)
+            assert np.array_equal(f, ref), (st, tile, zc)
 
 
 def test_checkpoint_restore(sc, oracle_mod):
@@ -210,16 +222,17 @@ def _storage_ulp(off, storage):
     return np.maximum(ulp, 2.0 ** -24 if storage == "f16" else 2.0 ** -133)
 
 
+@pytest.mark.parametrize("nx", [37, 40])
 @pytest.mark.parametrize("kernel", [1, 4])
 @pytest.mark.parametrize("storage", ["f16", "bf16"])
 @pytest.mark.parametrize("with_sink", [False, True])
-def test_reduced_precision_one_step(sc, oracle_mod, W, storage, with_sink, kernel):
+def test_reduced_precision_one_step(sc, oracle_mod, W, storage, with_sink, kernel, nx):
     """FP16/BF16 offset storage: one step equals the oracle on the same quantised input
     to within one storage ulp of the offset f - w_i (plus FP32 arithmetic). With a
     sink the oracle recomputes the sink's complement from the quantised input in FP64
     while the GPU keeps it quantised, so sinks and their neighbours get three ulps."""
     from paper_1701_03637_gb300.workloads import random_populations
-    nx, ny, nz = 37, 13, 11
+    ny, nz = 13, 11
     geom = dict(GEOMS["wall_planar_sink"])
     if not with_sink:
         geom.update(geometry=0)
