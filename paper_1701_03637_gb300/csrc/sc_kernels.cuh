@@ -41,6 +41,16 @@ __host__ __device__ constexpr int dir_z(int i) {
        : (i == 6 || i == 12 || i == 13 || i == 16 || i == 17) ? -1 : 0;
 }
 __host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+// e_y + 1 and e_z + 1 of all 19 directions in 2 bits each, for runtime direction indices.
+constexpr unsigned long long pack_dir(int axis) {
+  unsigned long long v = 0;
+  for (int i = 0; i < 19; ++i)
+    v |= (unsigned long long)((axis == 1 ? dir_y(i) : dir_z(i)) + 1) << (2 * i);
+  return v;
+}
+constexpr unsigned long long kDirY = pack_dir(1), kDirZ = pack_dir(2);
+__device__ __forceinline__ int dir_y_rt(int i) { return (int)((kDirY >> (2 * i)) & 3ull) - 1; }
+__device__ __forceinline__ int dir_z_rt(int i) { return (int)((kDirZ >> (2 * i)) & 3ull) - 1; }
 // Lattice weights (Sec. II A): 1/3 rest, 1/18 axis, 1/36 diagonal. In FP32 they are
 // chosen within two ulps of those values so that w0 + 6 w1 + 12 w2 == 1 exactly:
 // with the nearest floats the sum is 1 + 2^-26 and every collision would create
@@ -125,6 +135,11 @@ struct StBF16 {
 __host__ __device__ __forceinline__ int wrapi(int v, int n) {
   v %= n;
   return v < 0 ? v + n : v;
+}
+// Periodic wrap without a division when v is within one period of [0, n).
+__host__ __device__ __forceinline__ int wrap_near(int v, int n) {
+  v = v < 0 ? v + n : (v >= n ? v - n : v);
+  return (unsigned)v < (unsigned)n ? v : wrapi(v, n);
 }
 
 __device__ __forceinline__ bool solid_z(const LatDev& L, int z) { return z >= L.wall_z0 && z < L.wall_z1; }
@@ -653,8 +668,8 @@ struct TileRows {
   __device__ __forceinline__ void table(int p) {
     const int zp = wrapz(p);
     for (int R = threadIdx.x; R < NR; R += NT) {
-      const int ci = R / RH, r = R - ci * RH, i = ci % Q;
-      const int zs = wrapz(zp - dir_z(i)), ys = wrapi(y0 - 1 + r - dir_y(i), L.ny);
+      const int ci = R / RH, r = R - ci * RH, i = ci < Q ? ci : ci - Q;
+      const int zs = wrapz(zp - dir_z_rt(i)), ys = wrap_near(y0 - 1 + r - dir_y_rt(i), L.ny);
       sm.rowp[R] = src + ((long long)ci * L.np + (long long)zs * L.nxny + (long long)ys * L.nx);
     }
   }
@@ -663,8 +678,14 @@ struct TileRows {
   // rows cr0, cr0 + RS, ...; cx is that column's wrapped x.
   __device__ __forceinline__ void issue(int cx) {
     T* to = &sm.stage[0][0][0] + cr0 * SW + cj * E;
-#pragma unroll 4
-    for (int R = cr0; R < NR; R += RS, to += RS * SW) cp_async16(to, sm.rowp[R] + cx);
+    constexpr int PASSES = (NR + RS - 1) / RS;  // rows cr0 + k RS < NR for every k < PASSES - 1
+    if (cr0 < NR) {
+#pragma unroll
+      for (int k = 0; k < PASSES; ++k) {
+        const int R = cr0 + k * RS;
+        if (k < PASSES - 1 || R < NR) cp_async16(to + k * RS * SW, sm.rowp[R] + cx);
+      }
+    }
     cp_async_commit();
   }
 
