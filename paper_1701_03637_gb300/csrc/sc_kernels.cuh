@@ -348,14 +348,19 @@ __device__ __forceinline__ void relax(const LatDev& L, int c, float (&f)[Q], flo
   const float usq = __fmaf_rn(u[0], u[0], __fmaf_rn(u[1], u[1], __fmul_rn(u[2], u[2])));
   const float base = __fmaf_rn(-1.5f, usq, 1.0f);  // 1 - 1.5 u.u
   // f^eq_i = w_i rho (1 + 3 c.u + 4.5 (c.u)^2 - 1.5 u.u); opposite directions share
-  // the even part and differ in the sign of the odd part.
+  // the even part w rho (1 - 1.5 u.u) + 4.5 w rho (c.u)^2 and differ in the sign of
+  // the odd part 3 w rho c.u. The factors of w rho are formed once per weight class.
   f[0] = __fmaf_rn(om, __fsub_rn(__fmul_rn(__fmul_rn(kW0, rho), base), f[0]), f[0]);
+  const float wr1 = __fmul_rn(kW1, rho), wr2 = __fmul_rn(kW2, rho);
+  const float wb1 = __fmul_rn(wr1, base), wb2 = __fmul_rn(wr2, base);
+  const float w451 = __fmul_rn(4.5f, wr1), w452 = __fmul_rn(4.5f, wr2);
+  const float w31 = __fmul_rn(3.0f, wr1), w32 = __fmul_rn(3.0f, wr2);
   Unroll<0, 9>::run([&](auto kc) {
     constexpr int I = 1 + 2 * decltype(kc)::value, J = I + 1;
+    constexpr bool axis = I <= 6;
     const float cu = cdot<I>(u);
-    const float wr = __fmul_rn(wgt(I), rho);
-    const float ev = __fmul_rn(wr, __fmaf_rn(__fmul_rn(4.5f, cu), cu, base));
-    const float od = __fmul_rn(wr, __fmul_rn(3.0f, cu));
+    const float ev = __fmaf_rn(__fmul_rn(axis ? w451 : w452, cu), cu, axis ? wb1 : wb2);
+    const float od = __fmul_rn(axis ? w31 : w32, cu);
     f[I] = __fmaf_rn(om, __fsub_rn(__fadd_rn(ev, od), f[I]), f[I]);
     f[J] = __fmaf_rn(om, __fsub_rn(__fsub_rn(ev, od), f[J]), f[J]);
   });
@@ -373,29 +378,26 @@ __device__ __forceinline__ void collide(const LatDev& L, float (&fr)[Q], float (
   relax(L, 1, fb, rb, psb, ar, up);
 }
 
-// sum_i w_i Psi^c(x + e_i) e_i from a Psi ring; psi(c, plane slot, ly, lx).
-template <class PsiAt>
-__device__ __forceinline__ void force_sum(PsiAt psi, int c, int sm1, int s0, int sp1, int ly, int lx,
-                                          float (&a)[3]) {
-  a[0] = a[1] = a[2] = 0.f;
-  // opposite pairs (I, I+1): accumulate w_I (Psi(x+e_I) - Psi(x-e_I)) e_I
+// sum_i w_i Psi^c(x + e_i) e_i of both components from a Psi ring whose cells hold
+// (Psi^r, Psi^b); psi2(plane slot, ly, lx). Opposite pairs (I, I+1) contribute
+// w_I (Psi(x + e_I) - Psi(x - e_I)) e_I.
+template <class PsiAt2>
+__device__ __forceinline__ void force_sums(PsiAt2 psi2, int sm1, int s0, int sp1, int ly, int lx, float (&ar)[3],
+                                           float (&ab)[3]) {
+  ar[0] = ar[1] = ar[2] = 0.f;
+  ab[0] = ab[1] = ab[2] = 0.f;
   Unroll<0, 9>::run([&](auto kc) {
     constexpr int I = 1 + 2 * decltype(kc)::value;
     constexpr int ex = dir_x(I), ey = dir_y(I), ez = dir_z(I);
     const int sa = ez > 0 ? sp1 : (ez < 0 ? sm1 : s0);
     const int sb = ez > 0 ? sm1 : (ez < 0 ? sp1 : s0);
-    const float t = __fmul_rn(wgt(I), __fsub_rn(psi(c, sa, ly + ey, lx + ex), psi(c, sb, ly - ey, lx - ex)));
-    if (ex != 0) a[0] = ex > 0 ? __fadd_rn(a[0], t) : __fsub_rn(a[0], t);
-    if (ey != 0) a[1] = ey > 0 ? __fadd_rn(a[1], t) : __fsub_rn(a[1], t);
-    if (ez != 0) a[2] = ez > 0 ? __fadd_rn(a[2], t) : __fsub_rn(a[2], t);
+    const float2 pa = psi2(sa, ly + ey, lx + ex), pb = psi2(sb, ly - ey, lx - ex);
+    const float dr = __fsub_rn(pa.x, pb.x), db = __fsub_rn(pa.y, pb.y);
+    auto acc = [&](float& a, int e, float d) { a = __fmaf_rn(e > 0 ? wgt(I) : -wgt(I), d, a); };
+    if (ex != 0) { acc(ar[0], ex, dr); acc(ab[0], ex, db); }
+    if (ey != 0) { acc(ar[1], ey, dr); acc(ab[1], ey, db); }
+    if (ez != 0) { acc(ar[2], ez, dr); acc(ab[2], ez, db); }
   });
-}
-
-template <class PsiAt>
-__device__ __forceinline__ void force_sums(PsiAt psi, int sm1, int s0, int sp1, int ly, int lx, float (&ar)[3],
-                                           float (&ab)[3]) {
-  force_sum(psi, 0, sm1, s0, sp1, ly, lx, ar);
-  force_sum(psi, 1, sm1, s0, sp1, ly, lx, ab);
 }
 
 // ------------------------------------------------------------------ fused step, one x-y tile column
@@ -424,7 +426,7 @@ struct Tile {
   static_assert(NT % 32 == 0, "whole warps");
 
   struct Smem {
-    float ring[2][4][RH][RW];
+    float2 ring[4][RH][RW];  // (Psi^r, Psi^b) of plane slot, tile row + 1, tile column + 1
     double red[NW];
     uint32_t fin[2 * Q][NT];       // pulled populations of the own site, [c Q + i][thread]
     uint32_t fh[2 * Q][HS];        // pulled populations of the halo site, [c Q + i][thread]
@@ -503,8 +505,7 @@ struct Tile {
       pr = psi_of(rr);
       pb = psi_of(rb);
     }
-    sm.ring[0][slot][ty + 1][tx + 1] = pr;
-    sm.ring[1][slot][ty + 1][tx + 1] = pb;
+    sm.ring[slot][ty + 1][tx + 1] = make_float2(pr, pb);
     if (has_halo) {
       float hpr = 0.0f, hpb = 0.0f;
       if (hcl != SOLID) {
@@ -522,8 +523,7 @@ struct Tile {
         hpr = psi_of(hrr);
         hpb = psi_of(hrb);
       }
-      sm.ring[0][slot][hly + 1][hlx + 1] = hpr;
-      sm.ring[1][slot][hly + 1][hlx + 1] = hpb;
+      sm.ring[slot][hly + 1][hlx + 1] = make_float2(hpr, hpb);
     }
   }
 
@@ -538,10 +538,10 @@ struct Tile {
       for (int i = 0; i < Q; ++i) { fr[i] = rest_pop(i, rr); fb[i] = rest_pop(i, rb); }
     } else {
       float ar[3], ab[3];
-      auto psi = [&](int c, int sl, int ly, int lx) { return sm.ring[c][sl][ly + 1][lx + 1]; };
-      force_sums(psi, (z - 1) & 3, z & 3, (z + 1) & 3, ty, tx, ar, ab);
-      const float psr = sm.ring[0][z & 3][ty + 1][tx + 1], psb = sm.ring[1][z & 3][ty + 1][tx + 1];
-      collide(L, fr, fb, rr, rb, psr, psb, ar, ab);
+      auto psi2 = [&](int sl, int ly, int lx) { return sm.ring[sl][ly + 1][lx + 1]; };
+      force_sums(psi2, (z - 1) & 3, z & 3, (z + 1) & 3, ty, tx, ar, ab);
+      const float2 ps = sm.ring[z & 3][ty + 1][tx + 1];
+      collide(L, fr, fb, rr, rb, ps.x, ps.y, ar, ab);
     }
     store_site<S>(L, dst, s, fr, fb);
   }
@@ -622,7 +622,7 @@ struct TileRows {
 
   struct Smem {
     T stage[2 * Q][RH][SW];  // rows of plane p: [c Q + i][y - y0 + 1][x - x0 + E]
-    float ring[2][4][RH][RW];
+    float2 ring[4][RH][RW];  // (Psi^r, Psi^b) of plane slot, tile row + 1, tile column + 1
     const T* rowp[NR];       // source address of each staged row's column x = 0
     int chx[CH];             // wrapped x of chunk j
     double red[NW];
@@ -739,8 +739,7 @@ struct TileRows {
       pr = psi_of(rr);
       pb = psi_of(rb);
     }
-    sm.ring[0][slot][ty + 1][tx + 1] = pr;
-    sm.ring[1][slot][ty + 1][tx + 1] = pb;
+    sm.ring[slot][ty + 1][tx + 1] = make_float2(pr, pb);
     if (has_halo) {
       const int hcl = site_class(L, hx, hy, zp);
       float hpr = 0.0f, hpb = 0.0f;
@@ -759,8 +758,7 @@ struct TileRows {
         hpr = psi_of(hrr);
         hpb = psi_of(hrb);
       }
-      sm.ring[0][slot][hly + 1][hlx + 1] = hpr;
-      sm.ring[1][slot][hly + 1][hlx + 1] = hpb;
+      sm.ring[slot][hly + 1][hlx + 1] = make_float2(hpr, hpb);
     }
     return cls;
   }
@@ -774,10 +772,10 @@ struct TileRows {
       for (int i = 0; i < Q; ++i) { fr[i] = rest_pop(i, rr); fb[i] = rest_pop(i, rb); }
     } else {
       float ar[3], ab[3];
-      auto psi = [&](int c, int sl, int ly, int lx) { return sm.ring[c][sl][ly + 1][lx + 1]; };
-      force_sums(psi, (z - 1) & 3, z & 3, (z + 1) & 3, ty, tx, ar, ab);
-      const float psr = sm.ring[0][z & 3][ty + 1][tx + 1], psb = sm.ring[1][z & 3][ty + 1][tx + 1];
-      collide(L, fr, fb, rr, rb, psr, psb, ar, ab);
+      auto psi2 = [&](int sl, int ly, int lx) { return sm.ring[sl][ly + 1][lx + 1]; };
+      force_sums(psi2, (z - 1) & 3, z & 3, (z + 1) & 3, ty, tx, ar, ab);
+      const float2 ps = sm.ring[z & 3][ty + 1][tx + 1];
+      collide(L, fr, fb, rr, rb, ps.x, ps.y, ar, ab);
     }
     store_site<S>(L, dst, s, fr, fb);
   }

@@ -228,9 +228,11 @@ def _storage_ulp(off, storage):
 @pytest.mark.parametrize("with_sink", [False, True])
 def test_reduced_precision_one_step(sc, oracle_mod, W, storage, with_sink, kernel, nx):
     """FP16/BF16 offset storage: one step equals the oracle on the same quantised input
-    to within one storage ulp of the offset f - w_i (plus FP32 arithmetic). With a
-    sink the oracle recomputes the sink's complement from the quantised input in FP64
-    while the GPU keeps it quantised, so sinks and their neighbours get three ulps."""
+    to within one storage ulp of the offset f - w_i plus the FP32 arithmetic bound of
+    the FP32 one-step test (1e-6 relative; it dominates where f is within a few FP32
+    ulps of w_i, whose offset has a tiny storage ulp). With a sink the oracle
+    recomputes the sink's complement from the quantised input in FP64 while the GPU
+    keeps it quantised, so sinks and their neighbours get three ulps."""
     from paper_1701_03637_gb300.workloads import random_populations
     ny, nz = 13, 11
     geom = dict(GEOMS["wall_planar_sink"])
@@ -253,7 +255,9 @@ def test_reduced_precision_one_step(sc, oracle_mod, W, storage, with_sink, kerne
         near[5:10] = True  # sink plane 7 and two planes either side
         k[:, :, near] = 3.0
     fluid = np.broadcast_to(o.site_class() == 0, fo.shape)
-    assert np.all((err <= k * ulp + 1e-7 * np.abs(fo))[fluid])
+    ratio = np.where(fluid, err / (k * ulp + 1e-6 * np.abs(fo)), 0.0)
+    worst = np.unravel_index(np.argmax(ratio), ratio.shape)
+    assert ratio.max() <= 1.0, (float(ratio.max()), worst, float(fg[worst]), float(fo[worst]), float(ulp[worst]))
 
 
 def test_full_size_sampled_windows(sc, oracle_mod):
