@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--zchunk", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="keep the automatic kernel configuration")
     ap.add_argument("--requests", type=int, default=40, help="serve workload: requests in the stream")
     ap.add_argument("--rate", type=float, default=20.0, help="serve workload: arrivals per second")
     return ap.parse_args()
@@ -75,9 +76,9 @@ def source_digest():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload_name, storage):
+def profiled_traffic(workload_name, storage, tile=None, zchunk=None):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on the
-    current kernel source and this workload; None otherwise."""
+    current kernel source, this workload and this launch configuration; None otherwise."""
     try:
         lines = open(PROFILE_FILE).read().splitlines()
     except OSError:
@@ -89,10 +90,17 @@ def profiled_traffic(workload_name, storage):
             kv[k.strip()] = v.strip().strip("`")
     if kv.get("source_digest") != source_digest() or kv.get("workload") != workload_name or kv.get("storage") != storage:
         return None
+    if tile is not None and (kv.get("tile") != tile or kv.get("zchunk") != str(zchunk)):
+        return None
     try:
         return float(kv["dram_bytes_per_launch"])
     except (KeyError, ValueError):
         return None
+
+
+def launch_cfg(lat):
+    info = lat.launch_info()
+    return f"{info['tile_x']}x{info['tile_y']}", info["zchunk"]
 
 
 def measured_peak_hbm():
@@ -250,6 +258,9 @@ def run_ours(args):
     n = params["nx"] * params["ny"] * params["nz"]
     lat = sc.Lattice(params)
     lat.init(init)
+    tuned = None
+    if not args.tile and not args.zchunk and not args.no_tune:
+        tuned = lat.tune(trials=5)  # untimed; leaves the state unchanged
     stream = torch.cuda.current_stream()
     lat.step(args.warmup)
     torch.cuda.synchronize()
@@ -283,7 +294,7 @@ def run_ours(args):
     peak, peak_kind = measured_peak_hbm()
     achieved = BYTES_PER_SITE[args.storage] * n / step_s / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": profiled_traffic(args.workload, args.storage),
+            "traffic": profiled_traffic(args.workload, args.storage, *launch_cfg(lat)),
             "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
             "algorithmic_bytes_per_site": BYTES_PER_SITE[args.storage]}
 
@@ -339,7 +350,8 @@ def run_ours(args):
                "config": {"workload": describe(args.workload, params, args.storage),
                           "sites": n, "lattices_per_gpu": 1, "l2": "inputs larger than L2 (no flush)",
                           "tile": f"{info['tile_x']}x{info['tile_y']}", "zchunk": info["zchunk"],
-                          "ctas": info["ctas"], "parallelism": f"independent replicas x{world}"},
+                          "ctas": info["ctas"], "staging": info["staging"],
+                          "autotuned": tuned is not None, "parallelism": f"independent replicas x{world}"},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
                "clocks": clk, "diag": {k: d[k] for k in ("mass_r", "mass_b", "evaporated_mass", "radius")}}
         print(json.dumps(out))

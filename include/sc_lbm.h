@@ -179,6 +179,13 @@ int sc_lbm_diagnostics_noalloc(sc_lbm* h, double* out_dev);
    staging (SC_STAGING_THREAD or SC_STAGING_ROWS). Any output pointer may be NULL. */
 int sc_lbm_launch_info(sc_lbm* h, int32_t* tile_x, int32_t* tile_y, int32_t* zchunk, int64_t* ctas,
                        int32_t* staging);
+/* Autotuner of the step kernel: times `trials` launches of every tile shape x
+   z-chunk length (automatic, 16, 32, 64 planes) and keeps the fastest for the
+   following steps; reports the tile (entry + 1 of sc_tile_list) and planes per
+   CTA. Trial launches read the current state and write only the buffer the next
+   step overwrites, booking their evaporated mass in scratch, so the state and
+   the bookkeeping are unchanged. Synchronous. No counterpart in the paper. */
+int sc_lbm_tune(sc_lbm* h, int32_t trials, int32_t* tile, int32_t* zchunk);
 /* Bytes one sc_lbm_diagnostics / sc_lbm_profile call copies device-to-host. */
 int sc_lbm_diag_bytes(sc_lbm* h, size_t* bytes);
 /* Number of compiled tile shapes and their extents. */

@@ -209,6 +209,13 @@ class Lattice:
         check(_lib().sc_lbm_diag_bytes(self._h, C.byref(b)))
         return int(b.value)
 
+    def tune(self, trials: int = 3) -> dict:
+        """Time every tile shape and z-chunk length on this lattice and keep the fastest
+        (the state and bookkeeping are unchanged)."""
+        t, z = C.c_int32(), C.c_int32()
+        check(_lib().sc_lbm_tune(self._h, int(trials), C.byref(t), C.byref(z)))
+        return dict(tile=t.value, zchunk=z.value)
+
     def launch_info(self) -> dict:
         tx, ty, zc, n, st = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int64(), C.c_int32()
         check(_lib().sc_lbm_launch_info(self._h, C.byref(tx), C.byref(ty), C.byref(zc), C.byref(n), C.byref(st)))

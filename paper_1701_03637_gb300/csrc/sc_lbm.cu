@@ -495,6 +495,51 @@ struct sc_lbm {
 
 namespace {
 
+// Launch configuration of the persistent step for one tile shape.
+struct LaunchCfg {
+  int tile, cols_x, cols, nch, grid;
+};
+
+// Persistent grid of every resident CTA slot (at most the handle's
+// evaporated-mass slots). The z chunk count trades rounds (ceil(items / G))
+// against the two extra planes each item stages; zchunk > 0 fixes the chunk
+// length instead.
+int plan_launch(const sc_params* p, const Layout& l, int tile, int zchunk, LaunchCfg* c) {
+  int dev = 0, sms = 1;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int occ = step_ops(p->storage, tile, l.rows).occupancy();
+  if (occ < 1) return fail(SC_ECUDA, "the step kernel cannot be made resident: %s", cudaGetErrorString(cudaGetLastError()));
+  c->tile = tile;
+  c->cols_x = (p->nx + kTileX[tile] - 1) / kTileX[tile];
+  c->cols = c->cols_x * ((p->ny + kTileY[tile] - 1) / kTileY[tile]);
+  const long long slots = std::min<long long>((long long)sms * occ, l.nslots), cols = c->cols;
+  long long best_nch = 1;
+  if (zchunk > 0) {
+    best_nch = (p->nz + zchunk - 1) / zchunk;
+  } else {
+    double best = 1e300;
+    for (long long nch = 1; nch <= p->nz; ++nch) {
+      const long long rounds = (cols * nch + slots - 1) / slots;
+      const double cost = (double)rounds * ((double)((p->nz + nch - 1) / nch) + 2.0);
+      if (cost < best * (1.0 - 1e-9)) { best = cost; best_nch = nch; }
+    }
+  }
+  c->nch = (int)best_nch;
+  c->grid = (int)std::max(1LL, std::min<long long>(slots, cols * best_nch));
+  return SC_OK;
+}
+
+void apply_launch(sc_lbm* h, const LaunchCfg& c) {
+  h->lay.tile = c.tile;
+  h->lay.tx = kTileX[c.tile];
+  h->lay.ty = kTileY[c.tile];
+  h->lay.cols_x = c.cols_x;
+  h->lay.cols = c.cols;
+  h->nch = c.nch;
+  h->grid = c.grid;
+}
+
 int launch_one(sc_lbm* h, cudaStream_t st) {
   const int src = h->cur, dst = 1 - h->cur;
   StepArgs a{h->L, h->pop(src), h->pop(dst), h->evap(), h->lay.cols_x, h->lay.cols, h->nch, h->grid, st};
@@ -636,37 +681,14 @@ static int create_common(const sc_params* p, void* stream, void* buf, bool owns,
   h->base = (char*)buf;
   h->owns = owns;
   h->cur = 0;
-  int dev = 0, sms = 1;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e != cudaSuccess) {
+  LaunchCfg cfg;
+  int rc0 = plan_launch(p, h->lay, h->lay.tile, p->zchunk, &cfg);
+  if (rc0) {
     sc_lbm_destroy(h);
-    return fail(SC_ECUDA, "device query failed: %s", cudaGetErrorString(e));
+    return rc0;
   }
-  // Persistent grid of every resident CTA slot. The z chunk count trades rounds
-  // (ceil(items / G)) against the two extra planes each item stages; a caller
-  // zchunk > 0 fixes the chunk length instead.
-  const int occ = step_ops(p->storage, h->lay.tile, h->lay.rows).occupancy();
-  if (occ < 1) {
-    sc_lbm_destroy(h);
-    return fail(SC_ECUDA, "the step kernel cannot be made resident: %s", cudaGetErrorString(cudaGetLastError()));
-  }
-  const long long slots = std::min<long long>((long long)sms * occ, h->lay.nslots);
-  const long long cols = h->lay.cols;
-  long long best_nch = 1;
-  if (p->zchunk > 0) {
-    best_nch = (p->nz + p->zchunk - 1) / p->zchunk;
-  } else {
-    double best = 1e300;
-    for (long long nch = 1; nch <= p->nz; ++nch) {
-      const long long rounds = (cols * nch + slots - 1) / slots;
-      const double cost = (double)rounds * ((double)((p->nz + nch - 1) / nch) + 2.0);
-      if (cost < best * (1.0 - 1e-9)) { best = cost; best_nch = nch; }
-    }
-  }
-  h->nch = (int)best_nch;
-  h->grid = (int)std::max(1LL, std::min<long long>(slots, cols * best_nch));
-  e = cudaMallocHost((void**)&h->h_diag, sizeof(double) * p->nz * h->lay.diag_nsplit * kDiagFields);
+  apply_launch(h, cfg);
+  cudaError_t e = cudaMallocHost((void**)&h->h_diag, sizeof(double) * p->nz * h->lay.diag_nsplit * kDiagFields);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&h->h_evap, sizeof(double) * h->lay.nslots);
   if (e != cudaSuccess) {
     sc_lbm_destroy(h);
@@ -973,6 +995,51 @@ int sc_lbm_launch_info(sc_lbm* h, int32_t* tx, int32_t* ty, int32_t* zchunk, int
   if (ty) *ty = h->lay.ty;
   if (zchunk) *zchunk = (int32_t)((h->p.nz + h->nch - 1) / h->nch);
   if (ctas) *ctas = h->grid;
+  return SC_OK;
+}
+
+int sc_lbm_tune(sc_lbm* h, int32_t trials, int32_t* tile, int32_t* zchunk) {
+  if (!h) return fail(SC_EINVAL, "NULL handle");
+  if (trials < 1) trials = 3;
+  // trial launches book their evaporated mass in the read-out staging area
+  double* scratch = (double*)h->stage();
+  const long long scratch_slots = h->lay.stage_n;  // 2 * stage_n floats
+  const LaunchCfg saved{h->lay.tile, h->lay.cols_x, h->lay.cols, h->nch, h->grid};
+  LaunchCfg best = saved;
+  float best_ms = 1e30f;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  static const int kZc[] = {0, 16, 32, 64};
+  int rc = SC_OK;
+  std::vector<std::pair<int, int>> seen;
+  for (int t = 0; t < kNumTiles && rc == SC_OK; ++t)
+    for (int zc : kZc) {
+      LaunchCfg c;
+      if (plan_launch(&h->p, h->lay, t, zc, &c) != SC_OK || c.grid > scratch_slots) continue;
+      if (std::find(seen.begin(), seen.end(), std::make_pair(t, c.nch)) != seen.end()) continue;
+      seen.push_back({t, c.nch});
+      StepArgs a{h->L, h->pop(h->cur), h->pop(1 - h->cur), scratch, c.cols_x, c.cols, c.nch, c.grid, h->stream};
+      const StepOps ops = step_ops(h->p.storage, t, h->lay.rows);
+      cudaError_t e = ops.launch(a);  // warm-up
+      if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+      for (int k = 0; k < trials && e == cudaSuccess; ++k) e = ops.launch(a);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      if (e != cudaSuccess) { rc = fail(SC_ECUDA, "tuning trial failed: %s", cudaGetErrorString(e)); break; }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best_ms) { best_ms = ms; best = c; }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  if (best.tile != saved.tile || best.nch != saved.nch || best.grid != saved.grid) {
+    apply_launch(h, best);
+    if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
+  }
+  if (tile) *tile = h->lay.tile + 1;
+  if (zchunk) *zchunk = (int32_t)((h->p.nz + h->nch - 1) / h->nch);
   return SC_OK;
 }
 

@@ -194,6 +194,29 @@ def test_tiles_and_chunks_give_identical_bits(sc, nx, stagings, storage):
             assert np.array_equal(f, ref), (st, tile, zc)
 
 
+def test_tuner_keeps_state_and_bits(sc):
+    """The single-lattice autotuner leaves state and bookkeeping untouched, and the
+    configuration it picks computes the same bits."""
+    from paper_1701_03637_gb300.workloads import droplet
+    params, init = droplet(40, 9.0, 3)
+    params.update(nx=40, ny=23, nz=19, wall_z0=0, wall_thickness=2)
+    init.update(cx=20.0, cy=11.0, cz=9.0, radius=6.0)
+    a, b = sc.Lattice(params), sc.Lattice(params)
+    a.init(init)
+    b.init(init)
+    a.step(5)
+    b.step(5)
+    f, d = a.read_populations(), a.diagnostics()
+    cfg = a.tune(trials=2)
+    assert 1 <= cfg["tile"] <= len(sc.tile_list())
+    assert np.array_equal(a.read_populations(), f) and a.diagnostics() == d
+    a.step(20)
+    b.step(20)
+    assert np.array_equal(a.read_populations(), b.read_populations())
+    da, db = a.diagnostics(), b.diagnostics()
+    assert abs(da["evaporated_mass"] - db["evaporated_mass"]) <= 1e-12 * max(1.0, abs(db["evaporated_mass"]))
+
+
 def test_checkpoint_restore(sc, oracle_mod):
     from paper_1701_03637_gb300.workloads import film_4x4x128
     params, init = film_4x4x128(rho_hi=0.7, rho_lo=0.04, rho_H=0.01)
