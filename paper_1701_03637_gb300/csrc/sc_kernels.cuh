@@ -234,26 +234,23 @@ __device__ __forceinline__ uint32_t pull_async(const LatDev& L, const typename S
   return hi;
 }
 
-// Density from the 19 populations of a site, summed pairwise (depth 5, so the
-// additions overlap) in one fixed order that every kernel uses; get(i) yields
-// population i, so values can be summed as they are loaded.
+// Density from the 19 populations of a site: opposite pairs (I, I+1) first, then
+// a balanced tree (depth 5, so the additions overlap), in one fixed order that
+// every kernel uses; get(i) yields population i, so values can be summed as they
+// are loaded.
 template <class Get>
 __device__ __forceinline__ float sum19_of(Get&& get) {
-  const float a0 = __fadd_rn(get(std::integral_constant<int, 0>()), get(std::integral_constant<int, 1>()));
-  const float a1 = __fadd_rn(get(std::integral_constant<int, 2>()), get(std::integral_constant<int, 3>()));
-  const float b0 = __fadd_rn(a0, a1);
-  const float a2 = __fadd_rn(get(std::integral_constant<int, 4>()), get(std::integral_constant<int, 5>()));
-  const float a3 = __fadd_rn(get(std::integral_constant<int, 6>()), get(std::integral_constant<int, 7>()));
-  const float b1 = __fadd_rn(a2, a3);
-  const float a4 = __fadd_rn(get(std::integral_constant<int, 8>()), get(std::integral_constant<int, 9>()));
-  const float a5 = __fadd_rn(get(std::integral_constant<int, 10>()), get(std::integral_constant<int, 11>()));
-  const float b2 = __fadd_rn(a4, a5);
-  const float a6 = __fadd_rn(get(std::integral_constant<int, 12>()), get(std::integral_constant<int, 13>()));
-  const float a7 = __fadd_rn(get(std::integral_constant<int, 14>()), get(std::integral_constant<int, 15>()));
-  const float b3 = __fadd_rn(a6, a7);
-  const float a8 = __fadd_rn(get(std::integral_constant<int, 16>()), get(std::integral_constant<int, 17>()));
-  const float b4 = __fadd_rn(a8, get(std::integral_constant<int, 18>()));
-  return __fadd_rn(__fadd_rn(__fadd_rn(b0, b1), __fadd_rn(b2, b3)), b4);
+  auto pair = [&](auto ic) {
+    constexpr int I = 1 + 2 * decltype(ic)::value;
+    return __fadd_rn(get(std::integral_constant<int, I>()), get(std::integral_constant<int, I + 1>()));
+  };
+  using std::integral_constant;
+  const float c0 = __fadd_rn(pair(integral_constant<int, 0>()), pair(integral_constant<int, 1>()));
+  const float c1 = __fadd_rn(pair(integral_constant<int, 2>()), pair(integral_constant<int, 3>()));
+  const float c2 = __fadd_rn(pair(integral_constant<int, 4>()), pair(integral_constant<int, 5>()));
+  const float c3 = __fadd_rn(pair(integral_constant<int, 6>()), pair(integral_constant<int, 7>()));
+  const float c4 = __fadd_rn(pair(integral_constant<int, 8>()), get(integral_constant<int, 0>()));
+  return __fadd_rn(__fadd_rn(__fadd_rn(c0, c1), __fadd_rn(c2, c3)), c4);
 }
 __device__ __forceinline__ float sum19(const float (&f)[Q]) {
   return sum19_of([&](auto ic) { return f[decltype(ic)::value]; });
@@ -295,16 +292,24 @@ __device__ __forceinline__ void store_site(const LatDev& L, typename S::T* __res
 }
 
 // Momentum sum_i f_i e_i of one component.
+// Momentum sum_i f_i e_i of one component from the differences of opposite
+// pairs, d = f_I - f_{I+1} (e_{I+1} = -e_I): each axis sums the five d whose
+// e_I has a component along it.
 __device__ __forceinline__ void momentum(const float (&f)[Q], float (&m)[3]) {
-  m[0] = m[1] = m[2] = 0.f;
-  Unroll<1, Q>::run([&](auto ic) {
-    constexpr int I = decltype(ic)::value;
-    if (dir_x(I) > 0) m[0] += f[I];
-    if (dir_x(I) < 0) m[0] -= f[I];
-    if (dir_y(I) > 0) m[1] += f[I];
-    if (dir_y(I) < 0) m[1] -= f[I];
-    if (dir_z(I) > 0) m[2] += f[I];
-    if (dir_z(I) < 0) m[2] -= f[I];
+  float d[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) d[k] = __fsub_rn(f[1 + 2 * k], f[2 + 2 * k]);
+  bool first[3] = {true, true, true};
+  Unroll<0, 9>::run([&](auto kc) {
+    constexpr int K = decltype(kc)::value, I = 1 + 2 * K;
+    constexpr int e[3] = {dir_x(I), dir_y(I), dir_z(I)};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (e[a] == 0) continue;
+      if (first[a]) m[a] = e[a] > 0 ? d[K] : -d[K];
+      else m[a] = e[a] > 0 ? __fadd_rn(m[a], d[K]) : __fsub_rn(m[a], d[K]);
+      first[a] = false;
+    }
   });
 }
 
