@@ -48,29 +48,25 @@ int wrap_host(int v, int n) { return ((v % n) + n) % n; }
 // ------------------------------------------------------------------ kernels
 
 // Persistent fused step; Rows selects the staged-rows marcher (TileRows) over
-// the per-thread one (Tile). The lattice is cut into tile columns
-// of TX x TY sites and z into nch chunks; item i = (chunk i / cols, column
-// i % cols). CTA b takes items b, b + G, b + 2G, ... so in every round the G
-// resident CTAs work on neighbouring columns of the same chunk in lock-step, and
-// a column's halo and shifted-pull sectors are read from DRAM once and then from
-// L2 by its neighbours. Chunks alternate their marching direction.
+// the per-thread one (Tile). CTA b marches items [starts[b], starts[b + 1]) of
+// the host-built work list (see plan_launch): tile columns of TX x TY sites and
+// z chunks, in every round the resident CTAs on neighbouring columns of the
+// same chunk in lock-step, so that a column's halo and shifted-pull sectors are
+// read from DRAM once and then from L2 by its neighbours.
 template <int TX, int TY, class S, bool Rows>
 __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 1 ? 512 / (TX * TY) : 1)
     k_step(const LatDev L, const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
-           double* __restrict__ evap_cum, int cols_x, int cols, int nch) {
+           double* __restrict__ evap_cum, int cols_x, const int4* __restrict__ items, const int* __restrict__ starts) {
   using TileT = std::conditional_t<Rows, TileRows<TX, TY, S>, Tile<TX, TY, S>>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   auto& sm = *reinterpret_cast<typename TileT::Smem*>(smem_raw);
   TileT t(L, sm, src, dst);
-  const long long items = (long long)cols * nch;
-  bool first = true;
-  for (long long it = blockIdx.x; it < items; it += gridDim.x) {
-    const int k = (int)(it / cols), c = (int)(it - (long long)k * cols);
-    const int zb = (int)((long long)k * L.nz / nch), ze = (int)((long long)(k + 1) * L.nz / nch);
-    if (!first) __syncthreads();  // the previous item's last reads of the ring
-    t.setup(c % cols_x, c / cols_x);
-    t.run(zb, ze, (k & 1) != 0);
-    first = false;
+  const int i0 = starts[blockIdx.x], i1 = starts[blockIdx.x + 1];
+  for (int it = i0; it < i1; ++it) {
+    const int4 w = items[it];  // tile column, first plane, end plane, downward
+    if (it > i0) __syncthreads();  // the previous item's last reads of the ring
+    t.setup(w.x % cols_x, w.x / cols_x);
+    t.run(w.y, w.z, w.w != 0);
   }
   if (L.geometry != 0) {
     const double e = t.block_evap();
@@ -322,7 +318,10 @@ struct StepArgs {
   const void* src;
   void* dst;
   double* evap;
-  int cols_x, cols, nch, G;
+  int cols_x;
+  const int4* items;
+  const int* starts;
+  int G;
   cudaStream_t st;
 };
 
@@ -334,7 +333,7 @@ constexpr size_t step_smem() {
 template <int TX, int TY, class S, bool Rows>
 cudaError_t launch_step(const StepArgs& a) {
   k_step<TX, TY, S, Rows><<<a.G, TX * TY, step_smem<TX, TY, S, Rows>(), a.st>>>(
-      a.L, (const typename S::T*)a.src, (typename S::T*)a.dst, a.evap, a.cols_x, a.cols, a.nch);
+      a.L, (const typename S::T*)a.src, (typename S::T*)a.dst, a.evap, a.cols_x, a.items, a.starts);
   return cudaGetLastError();
 }
 
@@ -388,7 +387,8 @@ struct Layout {
   long long nsites, stage_n;  // sites; staging floats per component
   long long units, nslots;
   int diag_nsplit;
-  size_t off_pop[2], off_stage, off_evap, off_diag, total;
+  long long cap_items;         // work-list capacity (items of any tile shape and schedule)
+  size_t off_pop[2], off_stage, off_evap, off_diag, off_items, off_starts, total;
 };
 
 int auto_tile(const sc_params* p) {
@@ -420,6 +420,11 @@ Layout make_layout(const sc_params* p) {
   l.off_stage = off; off += align256((size_t)2 * l.stage_n * sizeof(float));
   l.off_evap = off; off += align256((size_t)l.nslots * sizeof(double));
   l.off_diag = off; off += align256((size_t)p->nz * l.diag_nsplit * kDiagFields * sizeof(double));
+  // work list: at most one item per (column of the smallest tile, plane), plus one
+  // split per CTA of the balanced schedule (under 1 byte per site)
+  l.cap_items = (long long)((p->nx + 7) / 8) * ((p->ny + 3) / 4) * p->nz + kMaxCtas;
+  l.off_items = off; off += align256((size_t)l.cap_items * sizeof(int4));
+  l.off_starts = off; off += align256((size_t)(kMaxCtas + 1) * sizeof(int));
   l.total = off;
   return l;
 }
@@ -482,7 +487,7 @@ struct sc_lbm {
   double* h_diag;      // pinned
   double* h_evap;      // pinned
   int grid;  // CTAs of the persistent step
-  int nch;   // z chunks per tile column
+  int zmax;  // planes of the longest work item
   cudaGraphExec_t graph;
   int graph_len;
   int graph_cur;
@@ -491,19 +496,28 @@ struct sc_lbm {
   float* stage() const { return (float*)(base + lay.off_stage); }
   double* evap() const { return (double*)(base + lay.off_evap); }
   double* diag() const { return (double*)(base + lay.off_diag); }
+  int4* items() const { return (int4*)(base + lay.off_items); }
+  int* starts() const { return (int*)(base + lay.off_starts); }
 };
 
 namespace {
 
-// Launch configuration of the persistent step for one tile shape.
+// Launch configuration of the persistent step for one tile shape: the grid and
+// the work list, CTA b taking items [starts[b], starts[b + 1]).
 struct LaunchCfg {
-  int tile, cols_x, cols, nch, grid;
+  int tile, cols_x, cols, grid, zmax;
+  std::vector<int4> items;  // tile column, first plane, end plane, downward
+  std::vector<int> starts;
 };
 
-// Persistent grid of every resident CTA slot (at most the handle's
-// evaporated-mass slots). The z chunk count trades rounds (ceil(items / G))
-// against the two extra planes each item stages; zchunk > 0 fixes the chunk
-// length instead.
+// Plans the persistent grid (every resident CTA slot, at most the handle's
+// evaporated-mass slots) and its chunk-major work list: z is cut into nch
+// chunks, item i = (chunk i / cols, column i % cols), CTA b taking items b,
+// b + G, ...; in each round the resident CTAs work on neighbouring columns of
+// the same chunk in lock-step, so a column's halo and shifted-pull sectors come
+// from L2 for its neighbours. Chunks alternate their marching direction. The
+// chunk count trades rounds (ceil(items / G)) against the two halo planes each
+// item stages; zchunk > 0 fixes the chunk length instead.
 int plan_launch(const sc_params* p, const Layout& l, int tile, int zchunk, LaunchCfg* c) {
   int dev = 0, sms = 1;
   CK(cudaGetDevice(&dev));
@@ -513,36 +527,55 @@ int plan_launch(const sc_params* p, const Layout& l, int tile, int zchunk, Launc
   c->tile = tile;
   c->cols_x = (p->nx + kTileX[tile] - 1) / kTileX[tile];
   c->cols = c->cols_x * ((p->ny + kTileY[tile] - 1) / kTileY[tile]);
-  const long long slots = std::min<long long>((long long)sms * occ, l.nslots), cols = c->cols;
+  const long long slots = std::min<long long>((long long)sms * occ, l.nslots), cols = c->cols, nz = p->nz;
   long long best_nch = 1;
   if (zchunk > 0) {
-    best_nch = (p->nz + zchunk - 1) / zchunk;
+    best_nch = (nz + zchunk - 1) / zchunk;
   } else {
     double best = 1e300;
-    for (long long nch = 1; nch <= p->nz; ++nch) {
+    for (long long nch = 1; nch <= nz && cols * nch <= l.cap_items; ++nch) {
       const long long rounds = (cols * nch + slots - 1) / slots;
-      const double cost = (double)rounds * ((double)((p->nz + nch - 1) / nch) + 2.0);
+      const double cost = (double)rounds * ((double)((nz + nch - 1) / nch) + 2.0);
       if (cost < best * (1.0 - 1e-9)) { best = cost; best_nch = nch; }
     }
   }
-  c->nch = (int)best_nch;
-  c->grid = (int)std::max(1LL, std::min<long long>(slots, cols * best_nch));
+  const long long n = cols * best_nch;
+  if (n > l.cap_items) return fail(SC_EINVAL, "work list exceeds its capacity");
+  c->grid = (int)std::max(1LL, std::min<long long>(slots, n));
+  c->items.clear();
+  c->starts.clear();
+  c->zmax = 0;
+  for (long long b = 0; b < c->grid; ++b) {
+    c->starts.push_back((int)c->items.size());
+    for (long long it = b; it < n; it += c->grid) {
+      const long long k = it / cols, col = it - k * cols;
+      const int zb = (int)(k * nz / best_nch), ze = (int)((k + 1) * nz / best_nch);
+      c->items.push_back(make_int4((int)col, zb, ze, (int)(k & 1)));
+      c->zmax = std::max(c->zmax, ze - zb);
+    }
+  }
+  c->starts.push_back((int)c->items.size());
   return SC_OK;
 }
 
-void apply_launch(sc_lbm* h, const LaunchCfg& c) {
+// Makes c the handle's configuration and uploads its work list (synchronous).
+int apply_launch(sc_lbm* h, const LaunchCfg& c) {
+  CK(cudaMemcpyAsync(h->items(), c.items.data(), sizeof(int4) * c.items.size(), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->starts(), c.starts.data(), sizeof(int) * c.starts.size(), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
   h->lay.tile = c.tile;
   h->lay.tx = kTileX[c.tile];
   h->lay.ty = kTileY[c.tile];
   h->lay.cols_x = c.cols_x;
   h->lay.cols = c.cols;
-  h->nch = c.nch;
+  h->zmax = c.zmax;
   h->grid = c.grid;
+  return SC_OK;
 }
 
 int launch_one(sc_lbm* h, cudaStream_t st) {
   const int src = h->cur, dst = 1 - h->cur;
-  StepArgs a{h->L, h->pop(src), h->pop(dst), h->evap(), h->lay.cols_x, h->lay.cols, h->nch, h->grid, st};
+  StepArgs a{h->L, h->pop(src), h->pop(dst), h->evap(), h->lay.cols_x, h->items(), h->starts(), h->grid, st};
   cudaError_t e = step_ops(h->p.storage, h->lay.tile, h->lay.rows).launch(a);
   if (e != cudaSuccess) return fail(SC_ECUDA, "step launch failed: %s", cudaGetErrorString(e));
   h->cur = dst;
@@ -687,7 +720,11 @@ static int create_common(const sc_params* p, void* stream, void* buf, bool owns,
     sc_lbm_destroy(h);
     return rc0;
   }
-  apply_launch(h, cfg);
+  rc0 = apply_launch(h, cfg);
+  if (rc0) {
+    sc_lbm_destroy(h);
+    return rc0;
+  }
   cudaError_t e = cudaMallocHost((void**)&h->h_diag, sizeof(double) * p->nz * h->lay.diag_nsplit * kDiagFields);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&h->h_evap, sizeof(double) * h->lay.nslots);
   if (e != cudaSuccess) {
@@ -993,7 +1030,7 @@ int sc_lbm_launch_info(sc_lbm* h, int32_t* tx, int32_t* ty, int32_t* zchunk, int
   if (staging) *staging = h->lay.rows ? SC_STAGING_ROWS : SC_STAGING_THREAD;
   if (tx) *tx = h->lay.tx;
   if (ty) *ty = h->lay.ty;
-  if (zchunk) *zchunk = (int32_t)((h->p.nz + h->nch - 1) / h->nch);
+  if (zchunk) *zchunk = h->zmax;
   if (ctas) *ctas = h->grid;
   return SC_OK;
 }
@@ -1001,27 +1038,39 @@ int sc_lbm_launch_info(sc_lbm* h, int32_t* tx, int32_t* ty, int32_t* zchunk, int
 int sc_lbm_tune(sc_lbm* h, int32_t trials, int32_t* tile, int32_t* zchunk) {
   if (!h) return fail(SC_EINVAL, "NULL handle");
   if (trials < 1) trials = 3;
-  // trial launches book their evaporated mass in the read-out staging area
+  // trial launches book their evaporated mass in the read-out staging area and
+  // use the handle's work-list buffer; the chosen list is uploaded at the end
   double* scratch = (double*)h->stage();
   const long long scratch_slots = h->lay.stage_n;  // 2 * stage_n floats
-  const LaunchCfg saved{h->lay.tile, h->lay.cols_x, h->lay.cols, h->nch, h->grid};
-  LaunchCfg best = saved;
+  LaunchCfg best;
+  int rc = plan_launch(&h->p, h->lay, h->lay.tile, h->p.zchunk, &best);  // the current choice
+  if (rc) return rc;
   float best_ms = 1e30f;
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   static const int kZc[] = {0, 16, 32, 64};
-  int rc = SC_OK;
-  std::vector<std::pair<int, int>> seen;
+  std::vector<LaunchCfg> tried;
   for (int t = 0; t < kNumTiles && rc == SC_OK; ++t)
     for (int zc : kZc) {
       LaunchCfg c;
       if (plan_launch(&h->p, h->lay, t, zc, &c) != SC_OK || c.grid > scratch_slots) continue;
-      if (std::find(seen.begin(), seen.end(), std::make_pair(t, c.nch)) != seen.end()) continue;
-      seen.push_back({t, c.nch});
-      StepArgs a{h->L, h->pop(h->cur), h->pop(1 - h->cur), scratch, c.cols_x, c.cols, c.nch, c.grid, h->stream};
+      bool dup = false;
+      for (const LaunchCfg& o : tried)
+        dup = dup || (o.tile == c.tile && o.grid == c.grid && o.starts == c.starts && o.items.size() == c.items.size() &&
+                      std::equal(o.items.begin(), o.items.end(), c.items.begin(), [](const int4& u, const int4& v) {
+                        return u.x == v.x && u.y == v.y && u.z == v.z && u.w == v.w;
+                      }));
+      if (dup) continue;
+      tried.push_back(c);
+      cudaError_t e = cudaMemcpyAsync(h->items(), c.items.data(), sizeof(int4) * c.items.size(), cudaMemcpyHostToDevice,
+                                      h->stream);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->starts(), c.starts.data(), sizeof(int) * c.starts.size(), cudaMemcpyHostToDevice,
+                            h->stream);
+      StepArgs a{h->L, h->pop(h->cur), h->pop(1 - h->cur), scratch, c.cols_x, h->items(), h->starts(), c.grid, h->stream};
       const StepOps ops = step_ops(h->p.storage, t, h->lay.rows);
-      cudaError_t e = ops.launch(a);  // warm-up
+      if (e == cudaSuccess) e = ops.launch(a);  // warm-up
       if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
       for (int k = 0; k < trials && e == cudaSuccess; ++k) e = ops.launch(a);
       if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
@@ -1033,13 +1082,12 @@ int sc_lbm_tune(sc_lbm* h, int32_t trials, int32_t* tile, int32_t* zchunk) {
     }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  const int rc2 = apply_launch(h, best);  // also restores the work list after failed trials
   if (rc) return rc;
-  if (best.tile != saved.tile || best.nch != saved.nch || best.grid != saved.grid) {
-    apply_launch(h, best);
-    if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
-  }
+  if (rc2) return rc2;
+  if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
   if (tile) *tile = h->lay.tile + 1;
-  if (zchunk) *zchunk = (int32_t)((h->p.nz + h->nch - 1) / h->nch);
+  if (zchunk) *zchunk = h->zmax;
   return SC_OK;
 }
 
