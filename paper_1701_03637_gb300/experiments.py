@@ -1,0 +1,111 @@
+"""Experiments of arXiv:1701.03637 Sec. III run on the library's step.
+
+These drive the CUDA path through the public API and measure what the paper
+compares with its laws: the surface tension from the Laplace law (pressure
+jump across a droplet against 1/R, the sink closed), and the radius of an
+evaporating droplet with the spherical sink r >= R_H over time (Sec. III C).
+They only read fields and diagnostics; every time step runs in the library.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import Lattice
+
+CS2 = 1.0 / 3.0
+
+
+def bulk_pressure(rho_r, rho_b, G):
+    """Bulk pressure of the two-component Shan-Chen fluid with Psi = 1 - exp(-rho):
+    c_s^2 (rho^r + rho^b) + G c_s^2 Psi^r Psi^b (the force of Eq. (3) with
+    sum_i w_i e_i e_i = c_s^2 I)."""
+    pr = 1.0 - np.exp(-np.asarray(rho_r, np.float64))
+    pb = 1.0 - np.exp(-np.asarray(rho_b, np.float64))
+    return CS2 * (np.asarray(rho_r, np.float64) + rho_b) + G * CS2 * pr * pb
+
+
+def _droplet_params(n, G, tau, geometry=0, R_H=0.0, rho_H=0.03, storage="f32"):
+    c = n / 2.0
+    p = dict(nx=n, ny=n, nz=n, tau_r=tau, tau_b=tau, G=G, rho_H=rho_H, geometry=geometry, storage=storage)
+    if geometry == 2:
+        p.update(sphere_cx=c, sphere_cy=c, sphere_cz=c, R_H=R_H)
+    return p
+
+
+def _init(n, R, rho, seed):
+    c = n / 2.0
+    return dict(shape=1, cx=c, cy=c, cz=c, radius=R, rho_hi=rho[0], rho_lo=rho[1], noise_amp=1e-4, seed=seed)
+
+
+def surface_tension(radii=(8.0, 12.0, 16.0), margin=12, steps=4000, G=3.6, tau=1.0, rho=(0.7, 0.04), seed=5):
+    """Laplace test with the sink closed: for each initial radius a droplet in a
+    periodic box of edge 2 R + 2 margin equilibrates for `steps` steps; the
+    pressure jump between the centre and the box corner is fitted against 1/R
+    (R from the droplet volume). Returns gamma = slope / 2 and the fit data."""
+    inv_r, dp = [], []
+    for R0 in radii:
+        n = int(2 * R0 + 2 * margin)
+        lat = Lattice(_droplet_params(n, G, tau))
+        lat.init(_init(n, R0, rho, seed))
+        lat.step(steps)
+        rr, rb = lat.read_fields()
+        d = lat.diagnostics()
+        lat.close()
+        m = n // 2
+        inv_r.append(1.0 / d["radius"])
+        dp.append(float(bulk_pressure(rr[m, m, m], rb[m, m, m], G) - bulk_pressure(rr[0, 0, 0], rb[0, 0, 0], G)))
+    slope, icpt = np.polyfit(inv_r, dp, 1)
+    return dict(gamma=slope / 2.0, intercept=icpt, inv_radius=inv_r, pressure_jump=dp)
+
+
+def evaporating_droplet(n, R0, rho_H=0.01, G=3.6, tau=1.0, rho=(0.7, 0.04), equilibrate=2000, steps=20000,
+                        every=500, R_H=None, R_stop=4.0, seed=5, storage="f32"):
+    """A droplet equilibrates with the sink closed, then evaporates through the
+    spherical sink r >= R_H (default n/2 - 2) with rho^r = rho_H there. Returns
+    the radius series R(t) (t counted from opening the sink), the coexistence
+    densities at the start (rho^r at the centre, the r vapour density in the
+    shell R + 4 < r < R + 6, rho^b far outside) and R_H."""
+    R_H = n / 2.0 - 2.0 if R_H is None else R_H
+    eq = Lattice(_droplet_params(n, G, tau, storage=storage))
+    eq.init(_init(n, R0, rho, seed))
+    eq.step(equilibrate)
+    f = eq.read_populations()
+    rr, rb = eq.read_fields()
+    R_start = eq.diagnostics()["radius"]
+    eq.close()
+    c, m = n / 2.0, n // 2
+    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    r = np.sqrt((x - c) ** 2 + (y - c) ** 2 + (z - c) ** 2)
+    rho_ma0 = float(rr[m, m, m])
+    rho_mi0 = float(rr[(r > R_start + 4) & (r < R_start + 6)].mean())
+    rho_b_out = float(rb[0, 0, 0])
+    ev = Lattice(_droplet_params(n, G, tau, geometry=2, R_H=R_H, rho_H=rho_H, storage=storage))
+    ev.write_populations(f)
+    ts, Rs, fluxes = [0], [R_start], [0.0]
+    done = 0
+    while done < steps:
+        k = min(every, steps - done)
+        ev.step(k)
+        done += k
+        d = ev.diagnostics()
+        if d["status"] != 0:
+            raise RuntimeError(f"diagnostics status {d['status']} at step {done}")
+        ts.append(done)
+        Rs.append(d["radius"])
+        fluxes.append(d["evaporated_mass"])
+        if d["radius"] < R_stop:
+            break
+    ev.close()
+    return dict(t=np.asarray(ts, np.float64), R=np.asarray(Rs), evaporated_mass=np.asarray(fluxes), R_H=R_H,
+                rho_ma0=rho_ma0, rho_mi0=rho_mi0, rho_b_out=rho_b_out, rho_H=rho_H, G=G, n=n)
+
+
+def radius_rate(t, R, t0, t1):
+    """Mean dR/dt over [t0, t1] from a radius series (linear interpolation)."""
+    return (float(np.interp(t1, t, R)) - float(np.interp(t0, t, R))) / (t1 - t0)
+
+
+def equivalent_radius(droplet_sites: int) -> float:
+    return (3.0 * droplet_sites / (4.0 * math.pi)) ** (1.0 / 3.0)
