@@ -2,8 +2,9 @@
 
 These drive the CUDA path through the public API and measure what the paper
 compares with its laws: the surface tension from the Laplace law (pressure
-jump across a droplet against 1/R, the sink closed), and the radius of an
-evaporating droplet with the spherical sink r >= R_H over time (Sec. III C).
+jump across a droplet against 1/R, the sink closed), the radius of an
+evaporating droplet with the spherical sink r >= R_H over time (Sec. III C),
+and the interface position of an evaporating planar film (Sec. III B).
 They only read fields and diagnostics; every time step runs in the library.
 """
 from __future__ import annotations
@@ -109,3 +110,43 @@ def radius_rate(t, R, t0, t1):
 
 def equivalent_radius(droplet_sites: int) -> float:
     return (3.0 * droplet_sites / (4.0 * math.pi)) ** (1.0 / 3.0)
+
+
+def evaporating_film(nz=128, film_z=32, nxy=4, rho=(0.70, 0.04), rho_H=0.02, G=3.6, tau=1.0, equilibrate=20000,
+                     steps=1_000_000, every=10000, seed=0, storage="f32"):
+    """The planar film of Sec. III B: a wall of thickness 2 at z in {0, 1}, the
+    r-rich film below film_z, equilibrated with the sink closed, then evaporating
+    through the sink plane z = nz - 1 (rho^r = rho_H there). Returns the
+    interface position x_I(t) (t from opening the sink), the evaporated mass, the
+    coexistence densities of the equilibrated profile (rho^r in the liquid and
+    vapour plateaus, rho^b in the vapour) and x_H = nz - 1."""
+    base = dict(nx=nxy, ny=nxy, nz=nz, tau_r=tau, tau_b=tau, G=G, rho_H=rho_H, wall_z0=0, wall_thickness=2,
+                storage=storage)
+    eq = Lattice(dict(base, geometry=0))
+    eq.init(dict(shape=0, film_z=film_z, rho_hi=rho[0], rho_lo=rho[1], noise_amp=1e-4, seed=seed))
+    eq.step(equilibrate)
+    f = eq.read_populations()
+    rr, rb = eq.read_fields()
+    eq.close()
+    pr, pb = rr.mean(axis=(1, 2)), rb.mean(axis=(1, 2))
+    rho_ma = float(pr[4:film_z - 6].mean())
+    rho_mi = float(pr[film_z + 10:nz - 6].mean())
+    rho_b_vap = float(pb[film_z + 10:nz - 6].mean())
+    ev = Lattice(dict(base, geometry=1, sink_z0=nz - 1, sink_layers=1))
+    ev.write_populations(f)
+    d = ev.diagnostics()
+    ts, xs, em = [0], [d["interface_z"]], [0.0]
+    done = 0
+    while done < steps:
+        k = min(every, steps - done)
+        ev.step(k)
+        done += k
+        d = ev.diagnostics()
+        if d["status"] != 0:
+            raise RuntimeError(f"diagnostics status {d['status']} at step {done}")
+        ts.append(done)
+        xs.append(d["interface_z"])
+        em.append(d["evaporated_mass"])
+    ev.close()
+    return dict(t=np.asarray(ts, np.float64), x_I=np.asarray(xs), evaporated_mass=np.asarray(em), x_H=float(nz - 1),
+                rho_ma=rho_ma, rho_mi=rho_mi, rho_b_vap=rho_b_vap, rho_H=rho_H, G=G)
