@@ -30,7 +30,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-BYTES_PER_SITE = {"f32": 304, "f16": 152, "bf16": 152}  # read + write 2 x 19 populations
+BYTES_PER_SITE = {"f32": 304, "f16": 152, "bf16": 152, "f16s": 152}  # read + write 2 x 19 populations
 PROFILE_FILE = os.path.join(ROOT, "profiles", "k_step_droplet_128.md")
 
 
@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="droplet_128")
-    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16", "f16s"])
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--zchunk", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

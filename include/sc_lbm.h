@@ -59,6 +59,8 @@ extern "C" {
 #define SC_STORAGE_F32 0        /* FP32 populations */
 #define SC_STORAGE_F16 1        /* FP16 offsets f_i - w_i*rho0 (rho0 = 1), FP32 arithmetic */
 #define SC_STORAGE_BF16 2       /* BF16 offsets f_i - w_i*rho0, FP32 arithmetic */
+#define SC_STORAGE_F16_SCALED 3 /* FP16 of f_i / w_i (about rho: the same relative spacing in liquid
+                                   and vapour; not in the paper), FP32 arithmetic */
 
 #define SC_STAGING_AUTO 0       /* staged rows where nx allows, else per-thread pulls */
 #define SC_STAGING_THREAD 1     /* each thread copies its site's 38 pulls (any nx) */

@@ -15,7 +15,7 @@ from . import _native
 from ._native import Diag, Init, Params, ScError, build, check
 
 Q = 19
-STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
+STORAGE = {"f32": 0, "f16": 1, "bf16": 2, "f16s": 3}
 GEOMETRY = {"periodic": 0, "planar": 1, "sphere": 2}
 
 __all__ = ["Lattice", "Batch", "ScError", "build", "lattice_directions", "tile_list", "required_bytes", "Q"]

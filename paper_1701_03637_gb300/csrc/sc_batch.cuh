@@ -128,6 +128,7 @@ BatchOps pick_batch(int tile) {
 BatchOps batch_ops(int storage, int tile) {
   switch (storage) {
     case SC_STORAGE_F16: return pick_batch<StF16>(tile);
+    case SC_STORAGE_F16_SCALED: return pick_batch<StF16S>(tile);
     case SC_STORAGE_BF16: return pick_batch<StBF16>(tile);
     default: return pick_batch<StF32>(tile);
   }
@@ -383,7 +384,7 @@ extern "C" {
 int sc_batch_create(size_t arena_bytes, int32_t storage, void* stream, sc_batch** out) {
   if (!out) return fail(SC_EINVAL, "out is NULL");
   *out = nullptr;
-  if (storage < 0 || storage > 2) return fail(SC_EINVAL, "unknown storage %d", storage);
+  if (storage < 0 || storage > 3) return fail(SC_EINVAL, "unknown storage %d", storage);
   if (arena_bytes == 0) return fail(SC_EINVAL, "arena_bytes must be > 0");
   sc_batch* b = new (std::nothrow) sc_batch();
   if (!b) return fail(SC_ENOMEM, "host allocation failed");

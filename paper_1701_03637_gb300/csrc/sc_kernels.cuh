@@ -121,6 +121,19 @@ struct StF16 {
     return wt + __half2float(__ushort_as_half((unsigned short)(hi ? w >> 16 : w & 0xffffu)));
   }
 };
+// FP16 of the population scaled by its weight, g = f_i / w_i (about rho),
+// round to nearest even: the same relative spacing in the liquid and the vapour.
+struct StF16S {
+  using T = __half;
+  static __device__ __forceinline__ float ld(const T* p, float w) { return __fmul_rn(w, __half2float(__ldg(p))); }
+  static __device__ __forceinline__ float cv(T v, float w) { return __fmul_rn(w, __half2float(v)); }
+  // w is a compile-time weight at every call, so 1 / w folds to a constant
+  static __device__ __forceinline__ void st(T* p, float v, float w) { *p = __float2half_rn(__fmul_rn(v, 1.0f / w)); }
+  static __device__ __forceinline__ uint32_t pull_async(uint32_t* sm, const T* p) { return pull_async16(sm, p); }
+  static __device__ __forceinline__ float word(uint32_t w, uint32_t hi, float wt) {
+    return __fmul_rn(wt, __half2float(__ushort_as_half((unsigned short)(hi ? w >> 16 : w & 0xffffu))));
+  }
+};
 struct StBF16 {
   using T = __nv_bfloat16;
   static __device__ __forceinline__ float ld(const T* p, float w) { return w + __bfloat162float(__ldg(p)); }

@@ -371,6 +371,7 @@ StepOps pick_step(int tile) {
 StepOps step_ops(int storage, int tile, bool rows) {
   switch (storage) {
     case SC_STORAGE_F16: return rows ? pick_step<StF16, true>(tile) : pick_step<StF16, false>(tile);
+    case SC_STORAGE_F16_SCALED: return rows ? pick_step<StF16S, true>(tile) : pick_step<StF16S, false>(tile);
     case SC_STORAGE_BF16: return rows ? pick_step<StBF16, true>(tile) : pick_step<StBF16, false>(tile);
     default: return rows ? pick_step<StF32, true>(tile) : pick_step<StF32, false>(tile);
   }
@@ -441,7 +442,7 @@ int validate(const sc_params* p) {
   if (p->geometry == 2 && !(p->R_H > 0)) return fail(SC_EINVAL, "R_H must be > 0");
   if (p->wall_thickness < 0 || (p->wall_thickness > 0 && (p->wall_z0 < 0 || p->wall_z0 + p->wall_thickness > p->nz)))
     return fail(SC_EINVAL, "wall slab must lie inside [0, nz)");
-  if (p->storage < 0 || p->storage > 2) return fail(SC_EINVAL, "unknown storage %d", p->storage);
+  if (p->storage < 0 || p->storage > 3) return fail(SC_EINVAL, "unknown storage %d", p->storage);
   if (p->tile < 0 || p->tile > kNumTiles) return fail(SC_EINVAL, "tile index out of range");
   if (p->zchunk < 0) return fail(SC_EINVAL, "zchunk must be >= 0");
   if (p->staging < SC_STAGING_AUTO || p->staging > SC_STAGING_ROWS) return fail(SC_EINVAL, "unknown staging %d", p->staging);
@@ -597,6 +598,7 @@ int launch_canonical(sc_lbm* h, long long s0, long long s1, float* rho, long lon
 int canonical(sc_lbm* h, long long s0, long long s1, float* rho, long long rs, float* f, long long fs) {
   switch (h->p.storage) {
     case SC_STORAGE_F16: return launch_canonical<StF16>(h, s0, s1, rho, rs, f, fs);
+    case SC_STORAGE_F16_SCALED: return launch_canonical<StF16S>(h, s0, s1, rho, rs, f, fs);
     case SC_STORAGE_BF16: return launch_canonical<StBF16>(h, s0, s1, rho, rs, f, fs);
     default: return launch_canonical<StF32>(h, s0, s1, rho, rs, f, fs);
   }
@@ -616,6 +618,7 @@ int load(sc_lbm* h, long long s0, long long s1, int mode, const float* f, long l
          long long rs, const ShapeDev& sh) {
   switch (h->p.storage) {
     case SC_STORAGE_F16: return launch_load<StF16>(h, s0, s1, mode, f, fs, rho, rs, sh);
+    case SC_STORAGE_F16_SCALED: return launch_load<StF16S>(h, s0, s1, mode, f, fs, rho, rs, sh);
     case SC_STORAGE_BF16: return launch_load<StBF16>(h, s0, s1, mode, f, fs, rho, rs, sh);
     default: return launch_load<StF32>(h, s0, s1, mode, f, fs, rho, rs, sh);
   }
@@ -934,6 +937,7 @@ static int run_diag(sc_lbm* h) {
   int rc;
   switch (h->p.storage) {
     case SC_STORAGE_F16: rc = launch_diag<StF16>(h); break;
+    case SC_STORAGE_F16_SCALED: rc = launch_diag<StF16S>(h); break;
     case SC_STORAGE_BF16: rc = launch_diag<StBF16>(h); break;
     default: rc = launch_diag<StF32>(h);
   }
@@ -1015,6 +1019,7 @@ int sc_lbm_diagnostics_noalloc(sc_lbm* h, double* out_dev) {
   if (rc) return rc;
   switch (h->p.storage) {
     case SC_STORAGE_F16: rc = launch_diag_into<StF16>(h, part); break;
+    case SC_STORAGE_F16_SCALED: rc = launch_diag_into<StF16S>(h, part); break;
     case SC_STORAGE_BF16: rc = launch_diag_into<StBF16>(h, part); break;
     default: rc = launch_diag_into<StF32>(h, part);
   }

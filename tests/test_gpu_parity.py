@@ -240,14 +240,14 @@ def test_checkpoint_restore(sc, oracle_mod):
 
 
 def _storage_ulp(off, storage):
-    mant = 10 if storage == "f16" else 7
+    mant = 7 if storage == "bf16" else 10
     ulp = np.exp2(np.floor(np.log2(np.maximum(off, 1e-30))) - mant)
-    return np.maximum(ulp, 2.0 ** -24 if storage == "f16" else 2.0 ** -133)
+    return np.maximum(ulp, 2.0 ** -133 if storage == "bf16" else 2.0 ** -24)
 
 
 @pytest.mark.parametrize("nx", [37, 40])
 @pytest.mark.parametrize("kernel", [1, 4])
-@pytest.mark.parametrize("storage", ["f16", "bf16"])
+@pytest.mark.parametrize("storage", ["f16", "bf16", "f16s"])
 @pytest.mark.parametrize("with_sink", [False, True])
 def test_reduced_precision_one_step(sc, oracle_mod, W, storage, with_sink, kernel, nx):
     """FP16/BF16 offset storage: one step equals the oracle on the same quantised input
@@ -270,7 +270,11 @@ def test_reduced_precision_one_step(sc, oracle_mod, W, storage, with_sink, kerne
     g.step(1)
     o.step(1)
     fg, fo = g.read_populations(), o.populations()
-    ulp = _storage_ulp(np.abs(fo - W[None, :, None, None, None]), storage)
+    w = W[None, :, None, None, None]
+    if storage == "f16s":  # g = f / w stored: one FP16 ulp of g, times w
+        ulp = w * _storage_ulp(np.abs(fo) / w, storage)
+    else:
+        ulp = _storage_ulp(np.abs(fo - w), storage)
     err = np.abs(fg - fo)
     k = np.full(fo.shape, 1.01)
     if with_sink:

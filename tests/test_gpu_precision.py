@@ -2,7 +2,8 @@
 seeded droplet (the floating droplet of Sec. III C; radius / box = 0.1875 as in
 the 128^3 and 512^3 workloads): density L-infinity and L2 errors and the droplet
 size after N steps, for FP32 populations and for FP16 / BF16 offsets
-h_i = f_i - w_i rho0 (rho0 = 1) with FP32 arithmetic.
+h_i = f_i - w_i rho0 (rho0 = 1) with FP32 arithmetic, and for FP16 of the
+scaled populations g_i = f_i / w_i.
 
 Bounds: FP32 carries ~1e-7 relative rounding per step (parity bar 1e-4 after
 1000 steps). An FP16 offset store rounds h to 11 significant bits: |h| <= w_i
@@ -41,7 +42,7 @@ def _study(sc, oracle_mod, n, steps):
     orr, ob = o.fields()
     od = o.diagnostics()
     out = {}
-    for st in ("f32", "f16", "bf16"):
+    for st in ("f32", "f16", "bf16", "f16s"):
         g = sc.Lattice(dict(params, storage=st))
         g.init(init)
         g.step(steps)
@@ -69,7 +70,7 @@ def test_precision_vs_oracle_64(sc, oracle_mod):
     out = _study(sc, oracle_mod, 64, 1000)
     _record("64_1000", out)
     assert out["f32"]["linf"] < 1e-4
-    assert out["f16"]["linf"] < 3e-2 and out["bf16"]["linf"] < 0.25
+    assert out["f16"]["linf"] < 3e-2 and out["bf16"]["linf"] < 0.25 and out["f16s"]["linf"] < 3e-2
     assert out["f16"]["l2"] < 4e-3
     assert abs(out["f32"]["radius"] - out["f32"]["radius_oracle"]) < 1e-3
     assert abs(out["f16"]["radius"] - out["f16"]["radius_oracle"]) < 0.5
