@@ -290,7 +290,17 @@ __device__ __forceinline__ float sink_excess(const LatDev& L, const float (&fr)[
   return e;
 }
 
-__device__ __forceinline__ float psi_of(float rho) { return 1.0f - expf(-rho); }  // Eq. (4), rho0 = 1
+// Eq. (4) with rho0 = 1. Below rho = 2^-6, 1 - exp(-rho) would cancel, so Psi
+// is its Taylor series rho (1 - rho/2 (1 - rho/3 (1 - rho/4))) there (relative
+// truncation below rho^4 / 120 <= 5e-10): trace densities keep Psi ~ rho.
+__device__ __forceinline__ float psi_of(float rho) {
+  if (rho < 0.015625f) {
+    const float t = __fmaf_rn(-0.25f * rho, 1.0f / 3.0f, 1.0f / 3.0f);  // (1 - rho/4) / 3
+    const float u = __fmaf_rn(-rho * 0.5f, t, 0.5f);                     // (1 - rho/3 (...)) / 2
+    return __fmul_rn(rho, __fmaf_rn(-rho, u, 1.0f));
+  }
+  return 1.0f - expf(-rho);
+}
 
 template <class S>
 __device__ __forceinline__ void store_site(const LatDev& L, typename S::T* __restrict__ dst, int s,
@@ -358,11 +368,13 @@ __device__ __forceinline__ float cdot(const float (&u)[3]) {
 __device__ __forceinline__ void relax(const LatDev& L, int c, float (&f)[Q], float rho, float ps,
                                       const float (&a)[3], const float (&up)[3]) {
   const float om = c == 0 ? L.omega[0] : L.omega[1], tau = c == 0 ? L.tau[0] : L.tau[1];
-  const float sc = rho > 0.0f ? __fdiv_rn(tau, rho) : 0.0f;
-  const float gps = __fmul_rn(-L.G, ps);
+  // tau F / rho = (-g tau) (Psi / rho) a with Psi / rho <= 1, so a trace (or
+  // denormal) density cannot overflow the shift; rho = 0 takes u' itself
+  const float q = rho > 0.0f ? __fdiv_rn(ps, rho) : 0.0f;
+  const float gq = __fmul_rn(__fmul_rn(-L.G, tau), q);
   float u[3];
 #pragma unroll
-  for (int d = 0; d < 3; ++d) u[d] = __fmaf_rn(sc, __fmul_rn(gps, a[d]), up[d]);
+  for (int d = 0; d < 3; ++d) u[d] = __fmaf_rn(gq, a[d], up[d]);
   const float usq = __fmaf_rn(u[0], u[0], __fmaf_rn(u[1], u[1], __fmul_rn(u[2], u[2])));
   const float base = __fmaf_rn(-1.5f, usq, 1.0f);  // 1 - 1.5 u.u
   // f^eq_i = w_i rho (1 + 3 c.u + 4.5 (c.u)^2 - 1.5 u.u); opposite directions share

@@ -150,3 +150,58 @@ def evaporating_film(nz=128, film_z=32, nxy=4, rho=(0.70, 0.04), rho_H=0.02, G=3
     ev.close()
     return dict(t=np.asarray(ts, np.float64), x_I=np.asarray(xs), evaporated_mass=np.asarray(em), x_H=float(nz - 1),
                 rho_ma=rho_ma, rho_mi=rho_mi, rho_b_vap=rho_b_vap, rho_H=rho_H, G=G)
+
+
+def paper_flux_z(f, c, w, G):
+    """z flux of component r relative to the mixture, j^r = rho^r (U^r - U), with
+    the velocities of Eq. (velw) at tau = 1: U = (m^r + m^b + (F^r + F^b) / 2) /
+    (rho^r + rho^b) and U^r = (m^r + F^r + rho^r u') / (2 rho^r), u' the common
+    velocity and F^c = -g Psi^c(x) sum_i w_i Psi^cbar(x + e_i) e_i (Eq. (3),
+    periodic neighbours; solid sites have rho = Psi = 0). f: canonical populations
+    [2][19][z][y][x] (FP64); c, w: the library's direction table."""
+    rho = f.sum(axis=1)
+    m = np.tensordot(c.astype(np.float64).T, f, axes=([1], [1]))  # [3][2][z][y][x]
+    psi = -np.expm1(-rho)
+    acc = np.zeros((2, 3) + rho.shape[1:])
+    for i in range(1, len(w)):
+        e = c[i]
+        for cc in (0, 1):
+            pn = np.roll(psi[1 - cc], shift=(-int(e[2]), -int(e[1]), -int(e[0])), axis=(0, 1, 2))
+            for d in range(3):
+                if e[d]:
+                    acc[cc, d] += w[i] * pn * e[d]
+    F = -G * psi[:, None] * acc  # [2][3][...]
+    rr, rb = rho[0], rho[1]
+    rt = np.maximum(rr + rb, 1e-300)
+    up = (m[2, 0] + m[2, 1]) / rt  # tau_r = tau_b: the common velocity is the mixture momentum / mass
+    U = (m[2, 0] + m[2, 1] + 0.5 * (F[0, 2] + F[1, 2])) / rt
+    with np.errstate(divide="ignore", invalid="ignore"):
+        Ur = np.where(rr > 0, (m[2, 0] + F[0, 2] + rr * up) / (2.0 * rr), 0.0)
+    return np.where(rr > 0, rr * (Ur - U), 0.0)
+
+
+def fick_column(nz=128, nxy=4, rho_cbar=0.7, rho_H=0.001, G=3.6, tau=1.0, times=(3000, 10000), storage="f32"):
+    """The diffusion experiment of Sec. III A: a column of the other component
+    (rho^b = rho_cbar, rho^r = 0) between the evaporation boundary z = 0, which
+    holds rho^r = rho_H, and a wall of thickness 2 at the far end. Returns, at each
+    time, the xy-mean profiles of rho^r and rho^b and the z flux of r relative to
+    the mixture, rho^r (U^r - U) of Eqs. (flux) and (velw) (tau = 1), from the
+    canonical populations."""
+    p = dict(nx=nxy, ny=nxy, nz=nz, tau_r=tau, tau_b=tau, G=G, rho_H=rho_H, geometry=1, sink_z0=0, sink_layers=1,
+             wall_z0=nz - 2, wall_thickness=2, storage=storage)
+    lat = Lattice(p)
+    lat.init_fields(np.zeros((nz, nxy, nxy), np.float32), np.full((nz, nxy, nxy), rho_cbar, np.float32))
+    from . import lattice_directions
+    c, w = lattice_directions()
+    out = []
+    done = 0
+    for T in times:
+        lat.step(T - done)
+        done = T
+        f = lat.read_populations()  # [2][19][z][y][x]
+        rho = f.sum(axis=1)
+        j = paper_flux_z(f, c, w, G)
+        out.append(dict(t=T, rho_r=rho[0].mean(axis=(1, 2)), rho_b=rho[1].mean(axis=(1, 2)),
+                        flux=j.mean(axis=(1, 2))))
+    lat.close()
+    return out
