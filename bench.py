@@ -190,6 +190,24 @@ def host_cores():
         return os.cpu_count() or 1
 
 
+def max_over_ranks(v, world, device="cpu"):
+    """The largest of every rank's value (the slowest rank's time); world == 1
+    needs no process group."""
+    if world == 1:
+        return float(v)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(sites_per_rank, steps, world, ms_max):
+    """Whole-job MLUPS of independent replicas: every rank's site updates over
+    the slowest rank's time (weak scaling)."""
+    return sites_per_rank * steps * world / (ms_max * 1e-3) / 1e6
+
+
 def run_reference(args):
     """The oracle arm: FP64 plain-C oracle on the host cores, one oracle time step of a
     bounded crop of the workload per benchmark step."""
@@ -247,12 +265,8 @@ def run_ours(args):
         if world > 1:
             dist.barrier()
 
-    def max_over_ranks(v):
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def slowest(v):
+        return max_over_ranks(v, world, "cuda")
 
     params, init = workload(args.workload, args.storage, args.tile, args.zchunk)
     n = params["nx"] * params["ny"] * params["nz"]
@@ -283,13 +297,12 @@ def run_ours(args):
     t1 = time.time()
     sampler.stop()
     ms = e0.elapsed_time(e1)
-    ms_max = max_over_ranks(ms)
+    ms_max = slowest(ms)
     d = lat.diagnostics()
     if d["status"] != 0:
         raise RuntimeError(f"diagnostics status {d['status']} after the timed run")
 
-    sites_total = n * args.steps * world
-    value = sites_total / (ms_max * 1e-3) / 1e6
+    value = replica_value(n, args.steps, world, ms_max)
     step_s = ms * 1e-3 / args.steps
     peak, peak_kind = measured_peak_hbm()
     achieved = BYTES_PER_SITE[args.storage] * n / step_s / 1e9
@@ -324,7 +337,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         w1 = time.perf_counter()
         barrier()
-        wall = max_over_ranks(w1 - w0)
+        wall = slowest(w1 - w0)
         diag_bytes = ndiag * lat.diag_bytes()
         e2e = {"value": n * args.steps * world / wall / 1e6, "unit": "MLUPS",
                "h2d_bytes_per_step": 8 * n / args.steps,

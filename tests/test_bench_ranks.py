@@ -1,0 +1,50 @@
+"""The multi-GPU form of the benchmark is independent replicas (weak scaling):
+every rank advances its own lattice, the job's time is the slowest rank's, and
+the value counts every rank's site updates. Two gloo ranks on the CPU check the
+cross-rank reduction and the whole-job value."""
+import multiprocessing as mp
+import os
+import socket
+
+import pytest
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    ms = [120.0, 150.0][rank]  # rank 1 is the slow one
+    slow = bench.max_over_ranks(ms, world)
+    value = bench.replica_value(2 ** 21, 1000, world, slow)
+    q.put((rank, slow, value))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_take_the_slowest_time():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, slow, value in res:
+        assert slow == 150.0
+        assert value == pytest.approx(2 ** 21 * 1000 * 2 / 0.150 / 1e6)
+
+
+def test_single_rank_needs_no_process_group():
+    import bench
+    assert bench.max_over_ranks(7.5, 1) == 7.5
+    assert bench.replica_value(100, 10, 1, 1.0) == pytest.approx(1.0)
