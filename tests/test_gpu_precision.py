@@ -76,6 +76,30 @@ def test_precision_vs_oracle_64(sc, oracle_mod):
     assert abs(out["f16"]["radius"] - out["f16"]["radius_oracle"]) < 0.5
 
 
+def test_film_interface_vs_oracle(sc, oracle_mod):
+    """Interface position of the 4x4x128 film (paper densities 0.70 / 0.04,
+    rho_H = 0.02) after 2000 steps in every storage against the FP64 oracle."""
+    from paper_1701_03637_gb300.workloads import film_4x4x128
+    params, init = film_4x4x128(rho_hi=0.70, rho_lo=0.04, rho_H=0.02)
+    o = oracle_mod.Lattice(params)
+    o.init_shape(init)
+    o.step(2000)
+    od = o.diagnostics()
+    out = {}
+    for st in ("f32", "f16", "bf16", "f16s"):
+        g = sc.Lattice(dict(params, storage=st))
+        g.init(init)
+        g.step(2000)
+        d = g.diagnostics()
+        g.close()
+        out[st] = dict(interface_z=d["interface_z"], interface_z_oracle=od["interface_z"],
+                       error=abs(d["interface_z"] - od["interface_z"]),
+                       evaporated_mass=d["evaporated_mass"], evaporated_mass_oracle=od["evaporated_mass"])
+    _record("film_2000", out)
+    assert out["f32"]["error"] < 1e-3
+    assert out["f16"]["error"] < 0.5 and out["f16s"]["error"] < 0.5 and out["bf16"]["error"] < 2.0
+
+
 @pytest.mark.slow
 def test_precision_vs_oracle_128(sc, oracle_mod):
     if not os.environ.get("SC_RUN_SLOW"):
