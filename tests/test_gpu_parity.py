@@ -287,15 +287,19 @@ def test_reduced_precision_one_step(sc, oracle_mod, W, storage, with_sink, kerne
     assert ratio.max() <= 1.0, (float(ratio.max()), worst, float(fg[worst]), float(fo[worst]), float(ulp[worst]))
 
 
-def test_full_size_sampled_windows(sc, oracle_mod):
-    """128^3 droplet in the benchmark's launch configuration: one GPU step, checked at
-    sampled sites against the oracle run on a 7^3 window around each site (the step
-    reaches two sites, so the window's own periodic seam cannot reach the centre)."""
+@pytest.mark.parametrize("n,radius,seed,tuned", [(128, 24.0, 1, False), (128, 24.0, 1, True), (512, 96.0, 2, True)])
+def test_full_size_sampled_windows(sc, oracle_mod, n, radius, seed, tuned):
+    """The 128^3 and 512^3 droplets in the benchmark's launch configuration (the
+    autotuned one, as bench.py times it, and the automatic one): one GPU step,
+    checked at sampled sites against the oracle run on a 7^3 window around each
+    site (the step reaches two sites, so the window's own periodic seam cannot
+    reach the centre)."""
     from paper_1701_03637_gb300.workloads import droplet
-    n = 128
-    params, init = droplet(n, 24.0, 1)
+    params, init = droplet(n, radius, seed)
     g = sc.Lattice(params)
     g.init(init)
+    if tuned:
+        g.tune(trials=2)
     r0, b0 = g.read_fields()
     g.step(1)
     r1, b1 = g.read_fields()
@@ -303,8 +307,9 @@ def test_full_size_sampled_windows(sc, oracle_mod):
     assert abs((r1.sum(dtype=np.float64) + b1.sum(dtype=np.float64)) /
                (r0.sum(dtype=np.float64) + b0.sum(dtype=np.float64)) - 1) < 1e-6
     rng = np.random.default_rng(5)
-    pts = [(64, 64, 64), (64, 64, 64 + 24), (88, 64, 64), (10, 100, 126), (3, 5, 127), (7, 9, 0), (0, 0, 1),
-           (127, 127, 126)] + [tuple(int(v) for v in rng.integers(0, n, 3)) for _ in range(8)]
+    h, R = n // 2, int(radius)
+    pts = [(h, h, h), (h, h, h + R), (h + R, h, h), (10, n - 28, n - 2), (3, 5, n - 1), (7, 9, 0), (0, 0, 1),
+           (n - 1, n - 1, n - 2)] + [tuple(int(v) for v in rng.integers(0, n, 3)) for _ in range(8)]
     for (X, Y, Z) in pts:
         xs = np.arange(X - 3, X + 4) % n
         ys = np.arange(Y - 3, Y + 4) % n
