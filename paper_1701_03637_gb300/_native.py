@@ -47,7 +47,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with open(vscript, "w") as fh:
         fh.write("{ global: sc_*; local: *; };\n")
     tmp = LIB_PATH + f".tmp{os.getpid()}"
-    cmd = [_nvcc(), ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
+    # device code optimisation split over the host's cores (one translation unit)
+    cmd = [_nvcc(), ARCH, "-O3", "-lineinfo", "-std=c++17", f"--split-compile={min(os.cpu_count() or 1, 16)}",
+           "-Xcompiler", "-fPIC", "-shared",
            "-I", INCLUDE, "-Xlinker", f"--version-script={vscript}",
            *[os.path.join(CSRC, s) for s in SOURCES], "-o", tmp]
     if verbose:

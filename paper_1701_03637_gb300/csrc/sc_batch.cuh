@@ -121,6 +121,7 @@ BatchOps pick_batch(int tile) {
     case 0: return {&launch_batch<32, 8, S>, &occupancy_batch<32, 8, S>};
     case 1: return {&launch_batch<32, 4, S>, &occupancy_batch<32, 4, S>};
     case 2: return {&launch_batch<16, 8, S>, &occupancy_batch<16, 8, S>};
+    case 4: return {&launch_batch<64, 4, S>, &occupancy_batch<64, 4, S>};
     default: return {&launch_batch<8, 4, S>, &occupancy_batch<8, 4, S>};
   }
 }

@@ -37,9 +37,9 @@ int fail(int code, const char* fmt, ...) {
   } while (0)
 
 // Step kernel tile shapes (TX x TY sites per CTA).
-constexpr int kNumTiles = 4;
-constexpr int kTileX[kNumTiles] = {32, 32, 16, 8};
-constexpr int kTileY[kNumTiles] = {8, 4, 8, 4};
+constexpr int kNumTiles = 5;
+constexpr int kTileX[kNumTiles] = {32, 32, 16, 8, 64};
+constexpr int kTileY[kNumTiles] = {8, 4, 8, 4, 4};
 
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
@@ -364,6 +364,7 @@ StepOps pick_step(int tile) {
     case 0: return {&launch_step<32, 8, S, Rows>, &occupancy_step<32, 8, S, Rows>};
     case 1: return {&launch_step<32, 4, S, Rows>, &occupancy_step<32, 4, S, Rows>};
     case 2: return {&launch_step<16, 8, S, Rows>, &occupancy_step<16, 8, S, Rows>};
+    case 4: return {&launch_step<64, 4, S, Rows>, &occupancy_step<64, 4, S, Rows>};
     default: return {&launch_step<8, 4, S, Rows>, &occupancy_step<8, 4, S, Rows>};
   }
 }

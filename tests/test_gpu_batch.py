@@ -83,7 +83,7 @@ def test_members_match_the_lattices_stepped_alone(sc):
     b.close()
 
 
-@pytest.mark.parametrize("tile", [1, 2, 3, 4])
+@pytest.mark.parametrize("tile", [1, 2, 3, 4, 5])
 def test_every_tile_gives_the_same_bits(sc, tile):
     members = _members()[1:4]
     b = sc.Batch(1 << 29)

@@ -176,7 +176,7 @@ def test_tiles_and_chunks_give_identical_bits(sc, nx, stagings, storage):
         stagings = (0,)
     ref = None
     launches = [(st, tile, zc) for st in stagings
-                for tile, zc in [(1, 0), (2, 3), (3, 1), (4, 19), (1, 5), (2, 0), (3, 7)]]
+                for tile, zc in [(1, 0), (2, 3), (3, 1), (4, 19), (1, 5), (2, 0), (3, 7), (5, 0), (5, 4)]]
     for k, (st, tile, zc) in enumerate(launches):
         g = sc.Lattice(dict(params, tile=tile, zchunk=zc, staging=st))
         if st:
