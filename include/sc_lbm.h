@@ -67,6 +67,25 @@ extern "C" {
 #define SC_STAGING_ROWS 2       /* the CTA copies the tile's source rows as 16-byte chunks
                                    (nx a multiple of 4 for FP32, of 8 for FP16/BF16) */
 
+/* Population storage between steps (streaming, Sec. II A: each population moves to
+   the neighbour x + e_i, or back to x in the opposite direction where x + e_i is
+   solid). */
+#define SC_LAYOUT_TWO_LATTICE 0 /* two population lattices: each step pulls from one and
+                                   writes the other (one fused launch per step) */
+#define SC_LAYOUT_AA 1          /* one lattice updated in place (the AA pattern): half the
+                                   population memory. Steps alternate two forms: in the
+                                   even form population i arriving at x is kept where the
+                                   two-lattice pull reads it (at x - e_i, or at (opp(i), x)
+                                   next to a wall), in the odd form at (opp(i), x); a step
+                                   writes each post-collision population f*_j into the slot
+                                   that population opp(j) was read from. Since the force of
+                                   Eq. (3) needs Psi of the neighbours before any of them is
+                                   overwritten, each step is two launches: Psi of every site
+                                   into an FP32 (Psi^r, Psi^b) array (8 bytes per site), then
+                                   stream + sink + force + collision in place. Results are
+                                   bit-identical to SC_LAYOUT_TWO_LATTICE. Not for batch
+                                   members. */
+
 /* Physical and geometric parameters of one lattice (Sec. II; geometry of Sec. III). */
 typedef struct sc_params {
   int32_t nx, ny, nz;             /* lattice extent, each >= 1 */
@@ -81,6 +100,7 @@ typedef struct sc_params {
   int32_t tile;                   /* kernel tile choice: 0 = automatic, k > 0 = entry k-1 of sc_tile_list */
   int32_t zchunk;                 /* planes per CTA along z: 0 = automatic */
   int32_t staging;                /* SC_STAGING_*: how the step kernel gathers its pulls */
+  int32_t layout;                 /* SC_LAYOUT_*: two lattices or one updated in place */
 } sc_params;
 
 /* Seeded initial state: film or droplet with uniform noise. */
@@ -114,8 +134,8 @@ typedef struct sc_lbm sc_lbm;
 /* D3Q19 direction order used by every population array (c: [19][3]) and the weights. */
 int sc_lattice_directions(int32_t* c_host, double* w_host);
 
-/* Device bytes one lattice with these parameters needs (both population lattices,
-   diagnostics scratch). */
+/* Device bytes one lattice with these parameters needs (the population lattices of
+   its layout, the Psi array of the in-place layout, diagnostics scratch). */
 int sc_lbm_required_bytes(const sc_params* p, size_t* bytes);
 
 /* Create a lattice whose device memory the library allocates (cudaMalloc) and frees
@@ -139,8 +159,9 @@ int sc_lbm_init(sc_lbm* h, const sc_init* in);
    then the sink reset. Synchronous. */
 int sc_lbm_init_fields(sc_lbm* h, const float* rho_r_host, const float* rho_b_host);
 
-/* Advance nsteps time steps (asynchronous). Each step is one fused launch:
-   stream + sink reset + densities + Psi + force + collision. */
+/* Advance nsteps time steps (asynchronous). Each step is one fused launch
+   (stream + sink reset + densities + Psi + force + collision) with two lattices,
+   two launches in place (Psi, then the rest; SC_LAYOUT_AA). */
 int sc_lbm_step(sc_lbm* h, int64_t nsteps);
 
 /* Canonical densities into caller buffers (nx*ny*nz floats each). */
@@ -178,7 +199,9 @@ int sc_lbm_profile(sc_lbm* h, double* phi_host);
 int sc_lbm_diagnostics_noalloc(sc_lbm* h, double* out_dev);
 
 /* Kernel configuration in use: tile extents, planes per CTA, grid size and the
-   staging (SC_STAGING_THREAD or SC_STAGING_ROWS). Any output pointer may be NULL. */
+   staging (SC_STAGING_THREAD or SC_STAGING_ROWS). With SC_LAYOUT_AA: a row segment
+   of tile_x sites per CTA, tile_y = zchunk = 1, SC_STAGING_THREAD. Any output
+   pointer may be NULL. */
 int sc_lbm_launch_info(sc_lbm* h, int32_t* tile_x, int32_t* tile_y, int32_t* zchunk, int64_t* ctas,
                        int32_t* staging);
 /* Autotuner of the step kernel: times `trials` launches of every tile shape x
@@ -186,7 +209,9 @@ int sc_lbm_launch_info(sc_lbm* h, int32_t* tile_x, int32_t* tile_y, int32_t* zch
    following steps; reports the tile (entry + 1 of sc_tile_list) and planes per
    CTA. Trial launches read the current state and write only the buffer the next
    step overwrites, booking their evaporated mass in scratch, so the state and
-   the bookkeeping are unchanged. Synchronous. No counterpart in the paper. */
+   the bookkeeping are unchanged. Synchronous. No counterpart in the paper. With
+   SC_LAYOUT_AA there is no spare buffer and one configuration: it times nothing
+   and reports tile 0 and the current planes per CTA. */
 int sc_lbm_tune(sc_lbm* h, int32_t trials, int32_t* tile, int32_t* zchunk);
 /* Bytes one sc_lbm_diagnostics / sc_lbm_profile call copies device-to-host. */
 int sc_lbm_diag_bytes(sc_lbm* h, size_t* bytes);
@@ -215,7 +240,8 @@ void sc_batch_destroy(sc_batch* b);
    there. *slot names it in this batch; *lattice (may be NULL) is a handle for
    every sc_lbm_* call except sc_lbm_destroy and sc_lbm_set_stream: the batch owns
    it (sc_lbm_destroy on it does nothing). The member starts with unlimited steps
-   and must be initialised (sc_lbm_init / _init_fields / _write_populations). */
+   and must be initialised (sc_lbm_init / _init_fields / _write_populations).
+   Members use SC_LAYOUT_TWO_LATTICE (SC_EINVAL otherwise). */
 int sc_batch_add(sc_batch* b, const sc_params* p, int32_t* slot, sc_lbm** lattice);
 int sc_batch_lattice(sc_batch* b, int32_t slot, sc_lbm** lattice);
 /* Remove a member (synchronises the stream) and return its range to the arena. */

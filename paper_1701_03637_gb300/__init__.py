@@ -17,12 +17,13 @@ from ._native import Diag, Init, Params, ScError, build, check
 Q = 19
 STORAGE = {"f32": 0, "f16": 1, "bf16": 2, "f16s": 3}
 GEOMETRY = {"periodic": 0, "planar": 1, "sphere": 2}
+LAYOUT = {"two": 0, "aa": 1}
 
 __all__ = ["Lattice", "Batch", "ScError", "build", "lattice_directions", "tile_list", "required_bytes", "Q"]
 
 _PARAM_DEFAULTS = dict(tau_r=1.0, tau_b=1.0, G=3.6, rho_H=0.03, geometry=0, sink_z0=0, sink_layers=1,
                        sphere_cx=0.0, sphere_cy=0.0, sphere_cz=0.0, R_H=0.0, wall_z0=0, wall_thickness=0,
-                       storage=0, tile=0, zchunk=0, staging=0)
+                       storage=0, tile=0, zchunk=0, staging=0, layout=0)
 _INIT_DEFAULTS = dict(shape=0, film_z=0, cx=0.0, cy=0.0, cz=0.0, radius=0.0, rho_hi=1.0, rho_lo=0.03,
                       noise_amp=0.0, seed=0)
 
@@ -38,6 +39,8 @@ def make_params(params: dict) -> Params:
         p["storage"] = STORAGE[p["storage"]]
     if isinstance(p.get("geometry"), str):
         p["geometry"] = GEOMETRY[p["geometry"]]
+    if isinstance(p.get("layout"), str):
+        p["layout"] = LAYOUT[p["layout"]]
     return Params(**{k: p[k] for k, _ in Params._fields_})
 
 

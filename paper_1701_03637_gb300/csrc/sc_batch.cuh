@@ -429,6 +429,7 @@ int sc_batch_add(sc_batch* b, const sc_params* p, int32_t* slot, sc_lbm** lattic
   int rc = validate(p);
   if (rc) return rc;
   if (p->storage != b->storage) return fail(SC_EINVAL, "the lattice's storage differs from the batch's");
+  if (p->layout != SC_LAYOUT_TWO_LATTICE) return fail(SC_EINVAL, "batch members use the two-lattice layout");
   size_t bytes = 0;
   rc = sc_lbm_required_bytes(p, &bytes);
   if (rc) return rc;

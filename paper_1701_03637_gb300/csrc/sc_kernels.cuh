@@ -852,4 +852,62 @@ struct TileRows {
   }
 };
 
+// ------------------------------------------------------------------ in-place (AA) step
+//
+// One population lattice A updated in place. Between steps A holds, for every
+// non-solid site x and direction i, the population arriving at x in direction i
+// (the post-collision value of x - e_i, or x's own opposite one next to a wall):
+//   even form: at (i, x - e_i), or at (opp(i), x) where x - e_i is solid -- the
+//              slots the two-lattice pull reads (PullIdx::at);
+//   odd form:  at (opp(i), x).
+// A step reads the arrived populations of x and writes its post-collision f*_j
+// into the slot that population opp(j) came from. In the even form that slot is
+// where f*_j arrives in the odd form (x + e_j, or (j, x) when x + e_j is solid);
+// in the odd form it is (j, x), the even form's slot of f*_j. The slots a site
+// reads are exactly those it writes and belong to no other site, so no site's
+// update touches another's data. Only the force couples sites: every neighbour's
+// Psi must be formed before that neighbour is overwritten, so Psi comes from a
+// separate pass (k_aa_psi) into an (Psi^r, Psi^b) array.
+
+// Slot of the population arriving at the site of P in direction I.
+template <int I, bool ODD>
+__device__ __forceinline__ void aa_slot(const PullIdx& P, int& idx, int& d) {
+  if (ODD) {
+    idx = P.s;
+    d = opp(I);
+  } else {
+    P.template at<I>(idx, d);
+  }
+}
+
+// Arrived populations of the site of P (plain loads: the lattice is written in place).
+template <class S, bool ODD>
+__device__ __forceinline__ void aa_load(const LatDev& L, const typename S::T* A, const PullIdx& P, float (&fr)[Q],
+                                        float (&fb)[Q]) {
+  const long long cstride = (long long)Q * L.np;
+  Unroll<0, Q>::run([&](auto ic) {
+    constexpr int I = decltype(ic)::value;
+    int idx, d;
+    aa_slot<I, ODD>(P, idx, d);
+    const typename S::T* p = A + (long long)d * L.np + idx;
+    fr[I] = S::cv(p[0], wgt(I));
+    fb[I] = S::cv(p[cstride], wgt(I));
+  });
+}
+
+// f*_j into the slot population opp(j) was read from.
+template <class S, bool ODD>
+__device__ __forceinline__ void aa_store(const LatDev& L, typename S::T* A, const PullIdx& P, const float (&fr)[Q],
+                                         const float (&fb)[Q]) {
+  const long long cstride = (long long)Q * L.np;
+  Unroll<0, Q>::run([&](auto jc) {
+    constexpr int J = decltype(jc)::value;
+    int idx, d;
+    aa_slot<opp(J), ODD>(P, idx, d);
+    typename S::T* p = A + (long long)d * L.np + idx;
+    S::st(p, fr[J], wgt(J));
+    S::st(p + cstride, fb[J], wgt(J));
+  });
+}
+
 }  // namespace sclbm

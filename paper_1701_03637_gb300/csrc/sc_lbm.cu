@@ -74,6 +74,109 @@ __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 1 ? 512 / (TX * T
   }
 }
 
+// ------------------------------------------------------------------ in-place (AA) step
+//
+// Each step is k_aa_psi then k_aa_collide, both persistent grids over row
+// segments of kAAThreads sites (unit u: segment u % segs of row u / segs, row =
+// y + ny z; CTA b takes units b, b + G, ...), so the resident CTAs work on
+// neighbouring rows and the Psi rows of planes z - 1 .. z + 1 that a site's force
+// reads are L2 hits after their first read. The arithmetic is the two-lattice
+// step's (sum19, sink, psi_of, force_sums, collide), so the bits are the same.
+constexpr int kAAThreads = 128;
+
+struct AARow {
+  int x, y, z;
+  __device__ __forceinline__ AARow(const LatDev& L, long long u, int segs) {
+    const long long row = u / segs;
+    x = (int)(u - row * segs) * kAAThreads + (int)threadIdx.x;
+    y = (int)(row % L.ny);
+    z = (int)(row / L.ny);
+  }
+};
+
+// (Psi^r, Psi^b) of every site from its arrived populations (after the sink
+// reset of the densities); 0 at solid sites.
+template <class S, bool ODD>
+__global__ void __launch_bounds__(kAAThreads) k_aa_psi(const LatDev L, const typename S::T* A,
+                                                       float2* __restrict__ psi, int segs, long long units) {
+  for (long long u = blockIdx.x; u < units; u += gridDim.x) {
+    const AARow r(L, u, segs);
+    if (r.x >= L.nx) continue;
+    const int cls = site_class(L, r.x, r.y, r.z);
+    const PullIdx P(L, r.x, r.y, r.z);
+    float2 v = make_float2(0.f, 0.f);
+    if (cls != SOLID) {
+      float fr[Q], fb[Q];
+      aa_load<S, ODD>(L, A, P, fr, fb);
+      float rr = sum19(fr), rb = sum19(fb);
+      if (cls == SINK) sink_densities(L, rr, rb);
+      v = make_float2(psi_of(rr), psi_of(rb));
+    }
+    psi[P.s] = v;
+  }
+}
+
+// Stream (the arrived populations), sink, force from the Psi array, collision,
+// and the in-place store of f*; each CTA adds its evaporated mass to its slot.
+template <class S, bool ODD>
+__global__ void __launch_bounds__(kAAThreads, 4) k_aa_collide(const LatDev L, typename S::T* A,
+                                                              const float2* __restrict__ psi,
+                                                              double* __restrict__ evap_cum, int segs,
+                                                              long long units) {
+  double evap = 0.0;
+  for (long long u = blockIdx.x; u < units; u += gridDim.x) {
+    const AARow r(L, u, segs);
+    if (r.x >= L.nx) continue;
+    const int cls = site_class(L, r.x, r.y, r.z);
+    if (cls == SOLID) continue;
+    const PullIdx P(L, r.x, r.y, r.z);
+    float fr[Q], fb[Q];
+    aa_load<S, ODD>(L, A, P, fr, fb);
+    float rr = sum19(fr), rb = sum19(fb);
+    if (cls == SINK) {
+      // neither forced nor collided: f^eq at rest of the reset densities
+      evap += (double)sink_excess(L, fr);
+      sink_densities(L, rr, rb);
+#pragma unroll
+      for (int i = 0; i < Q; ++i) { fr[i] = rest_pop(i, rr); fb[i] = rest_pop(i, rb); }
+    } else {
+      const int nx = L.nx, ny = L.ny;
+      auto psi2 = [&](int zb, int yy, int xx) {
+        yy = yy < 0 ? yy + ny : (yy >= ny ? yy - ny : yy);
+        xx = xx < 0 ? xx + nx : (xx >= nx ? xx - nx : xx);
+        return psi[zb + yy * nx + xx];
+      };
+      float ar[3], ab[3];
+      force_sums(psi2, P.zs[2], P.zs[1], P.zs[0], r.y, r.x, ar, ab);  // planes z - 1, z, z + 1
+      const float2 ps = psi[P.s];
+      collide(L, fr, fb, rr, rb, ps.x, ps.y, ar, ab);
+    }
+    aa_store<S, ODD>(L, A, P, fr, fb);
+  }
+  if (L.geometry != 0) {
+    __shared__ double red[kAAThreads / 32];
+    double v = evap;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int k = 0; k < kAAThreads / 32; ++k) t += red[k];
+      evap_cum[blockIdx.x] += t;
+    }
+  }
+}
+
+// Arrived populations for the read-out kernels: the pull of the two-lattice
+// buffer or of the in-place lattice's even form, or the odd form's own slots.
+template <class S>
+__device__ __forceinline__ void arrived(const LatDev& L, const typename S::T* __restrict__ src, const PullIdx& P,
+                                        int odd, float (&fr)[Q], float (&fb)[Q]) {
+  if (odd) aa_load<S, true>(L, src, P, fr, fb);
+  else pull_full<S>(L, src, P, fr, fb);
+}
+
 __device__ __forceinline__ void site_of(const LatDev& L, long long s, int& x, int& y, int& z) {
   x = (int)(s % L.nx);
   y = (int)((s / L.nx) % L.ny);
@@ -85,7 +188,7 @@ __device__ __forceinline__ void site_of(const LatDev& L, long long s, int& x, in
 template <class S>
 __global__ void k_canonical(const LatDev L, const typename S::T* __restrict__ src, long long s0, long long s1,
                             float* __restrict__ rho_out, long long rho_stride, float* __restrict__ f_out,
-                            long long f_stride) {
+                            long long f_stride, int odd) {
   for (long long s = s0 + blockIdx.x * (long long)blockDim.x + threadIdx.x; s < s1;
        s += (long long)gridDim.x * blockDim.x) {
     int x, y, z;
@@ -97,7 +200,7 @@ __global__ void k_canonical(const LatDev L, const typename S::T* __restrict__ sr
       for (int i = 0; i < Q; ++i) fr[i] = fb[i] = 0.f;
     } else {
       const PullIdx P(L, x, y, z);
-      pull_full<S>(L, src, P, fr, fb);
+      arrived<S>(L, src, P, odd, fr, fb);
       rr = sum19(fr);
       rb = sum19(fb);
       if (cls == SINK) {
@@ -125,7 +228,7 @@ constexpr int kDiagThreads = 256;
 
 template <class S>
 __global__ void __launch_bounds__(kDiagThreads) k_diag(const LatDev L, const typename S::T* __restrict__ src,
-                                                       int nsplit, double* __restrict__ part) {
+                                                       int nsplit, double* __restrict__ part, int odd) {
   const int z = blockIdx.x, k = blockIdx.y;
   const int nxy = L.nx * L.ny;
   const int per = (nxy + nsplit - 1) / nsplit;
@@ -140,7 +243,7 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag(const LatDev L, const typ
       const int cls = site_class(L, x, y, z);
       const PullIdx P(L, x, y, z);
       float fr[Q], fb[Q];
-      pull_full<S>(L, src, P, fr, fb);
+      arrived<S>(L, src, P, odd, fr, fb);
       float rr = sum19(fr), rb = sum19(fb);
       double mr = rr;
       if (cls == SINK) {
@@ -385,12 +488,15 @@ size_t elem_size(int storage) { return storage == SC_STORAGE_F32 ? 4 : 2; }
 struct Layout {
   int tile, tx, ty, cols_x, cols;
   bool rows;                  // staged-rows step kernel (nx a multiple of a 16-byte chunk)
+  bool aa;                    // one population lattice updated in place (SC_LAYOUT_AA)
+  int aa_segs;                // row segments of kAAThreads sites per row (in place)
+  long long aa_units;         // row segments of the lattice (in place)
   long long np;               // array stride (elements)
   long long nsites, stage_n;  // sites; staging floats per component
   long long units, nslots;
   int diag_nsplit;
   long long cap_items;         // work-list capacity (items of any tile shape and schedule)
-  size_t off_pop[2], off_stage, off_evap, off_diag, off_items, off_starts, total;
+  size_t off_pop[2], off_psi, off_stage, off_evap, off_diag, off_items, off_starts, total;
 };
 
 int auto_tile(const sc_params* p) {
@@ -405,20 +511,26 @@ Layout make_layout(const sc_params* p) {
   l.tile = p->tile > 0 ? p->tile - 1 : auto_tile(p);
   l.tx = kTileX[l.tile];
   l.ty = kTileY[l.tile];
-  l.rows = p->staging == SC_STAGING_ROWS || (p->staging == SC_STAGING_AUTO && p->nx % (16 / es) == 0);
+  l.aa = p->layout == SC_LAYOUT_AA;
+  l.rows = !l.aa && (p->staging == SC_STAGING_ROWS || (p->staging == SC_STAGING_AUTO && p->nx % (16 / es) == 0));
   l.nsites = (long long)p->nx * p->ny * p->nz;
   l.np = round_up(l.nsites, 128 / es);  // each array starts 128-byte aligned
   l.stage_n = round_up(l.nsites, 64);
   l.cols_x = (p->nx + l.tx - 1) / l.tx;
   l.cols = l.cols_x * ((p->ny + l.ty - 1) / l.ty);
   l.units = (long long)l.cols * p->nz;
-  l.nslots = std::min(l.units, kMaxCtas);
+  l.aa_segs = (p->nx + kAAThreads - 1) / kAAThreads;
+  l.aa_units = (long long)l.aa_segs * p->ny * p->nz;
+  l.nslots = std::min(l.aa ? l.aa_units : l.units, kMaxCtas);
   const long long per_plane = (long long)p->nx * p->ny;
   l.diag_nsplit = (int)std::max(1LL, std::min<long long>((4LL * 152 + p->nz - 1) / p->nz, (per_plane + 1023) / 1024));
   const size_t pop = align256((size_t)(2 * Q * l.np * es));
   size_t off = 0;
   l.off_pop[0] = off; off += pop;
-  l.off_pop[1] = off; off += pop;
+  l.off_pop[1] = l.off_pop[0];
+  l.off_psi = off;
+  if (l.aa) off += align256((size_t)l.np * sizeof(float2));  // (Psi^r, Psi^b) per site
+  else { l.off_pop[1] = off; off += pop; }
   l.off_stage = off; off += align256((size_t)2 * l.stage_n * sizeof(float));
   l.off_evap = off; off += align256((size_t)l.nslots * sizeof(double));
   l.off_diag = off; off += align256((size_t)p->nz * l.diag_nsplit * kDiagFields * sizeof(double));
@@ -447,6 +559,7 @@ int validate(const sc_params* p) {
   if (p->tile < 0 || p->tile > kNumTiles) return fail(SC_EINVAL, "tile index out of range");
   if (p->zchunk < 0) return fail(SC_EINVAL, "zchunk must be >= 0");
   if (p->staging < SC_STAGING_AUTO || p->staging > SC_STAGING_ROWS) return fail(SC_EINVAL, "unknown staging %d", p->staging);
+  if (p->layout != SC_LAYOUT_TWO_LATTICE && p->layout != SC_LAYOUT_AA) return fail(SC_EINVAL, "unknown layout %d", p->layout);
   if (p->staging == SC_STAGING_ROWS && p->nx % (p->storage == SC_STORAGE_F32 ? 4 : 8) != 0)
     return fail(SC_EINVAL, "staged rows need nx to be a multiple of %d", p->storage == SC_STORAGE_F32 ? 4 : 8);
   if ((long long)p->nx > (1 << 20) || (long long)p->ny > (1 << 20) || (long long)p->nz > (1 << 20))
@@ -488,13 +601,16 @@ struct sc_lbm {
   double evap_offset;  // evaporated mass restored by sc_lbm_set_counters
   double* h_diag;      // pinned
   double* h_evap;      // pinned
-  int grid;  // CTAs of the persistent step
+  int grid;  // CTAs of the persistent step (in place: of k_aa_collide)
+  int grid_psi;  // CTAs of k_aa_psi
   int zmax;  // planes of the longest work item
   cudaGraphExec_t graph;
   int graph_len;
   int graph_cur;
   sc_batch* owner;  // batch whose arena holds this lattice (it destroys the handle)
   void* pop(int k) const { return base + lay.off_pop[k]; }
+  float2* psi() const { return (float2*)(base + lay.off_psi); }
+  int odd() const { return lay.aa && cur == 1 ? 1 : 0; }  // in-place lattice in its odd form
   float* stage() const { return (float*)(base + lay.off_stage); }
   double* evap() const { return (double*)(base + lay.off_evap); }
   double* diag() const { return (double*)(base + lay.off_diag); }
@@ -575,7 +691,70 @@ int apply_launch(sc_lbm* h, const LaunchCfg& c) {
   return SC_OK;
 }
 
+// In-place step launches for one storage type.
+template <class S>
+cudaError_t launch_aa(const sc_lbm* h, cudaStream_t st) {
+  using T = typename S::T;
+  const Layout& l = h->lay;
+  if (h->cur == 1) {
+    k_aa_psi<S, true><<<h->grid_psi, kAAThreads, 0, st>>>(h->L, (const T*)h->pop(0), h->psi(), l.aa_segs, l.aa_units);
+    k_aa_collide<S, true><<<h->grid, kAAThreads, 0, st>>>(h->L, (T*)h->pop(0), h->psi(), h->evap(), l.aa_segs,
+                                                          l.aa_units);
+  } else {
+    k_aa_psi<S, false><<<h->grid_psi, kAAThreads, 0, st>>>(h->L, (const T*)h->pop(0), h->psi(), l.aa_segs, l.aa_units);
+    k_aa_collide<S, false><<<h->grid, kAAThreads, 0, st>>>(h->L, (T*)h->pop(0), h->psi(), h->evap(), l.aa_segs,
+                                                           l.aa_units);
+  }
+  return cudaGetLastError();
+}
+
+template <class S>
+void occupancy_aa(int* psi_occ, int* collide_occ) {
+  int a = 0, b = 0, c = 0, d = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_aa_psi<S, false>, kAAThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_aa_psi<S, true>, kAAThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_aa_collide<S, false>, kAAThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d, k_aa_collide<S, true>, kAAThreads, 0);
+  *psi_occ = std::min(a, b);
+  *collide_occ = std::min(c, d);
+}
+
+// Grids of the in-place step: every resident CTA slot, the collision's at most
+// the evaporated-mass slots.
+int plan_aa(sc_lbm* h) {
+  int dev = 0, sms = 1, po = 0, co = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  switch (h->p.storage) {
+    case SC_STORAGE_F16: occupancy_aa<StF16>(&po, &co); break;
+    case SC_STORAGE_F16_SCALED: occupancy_aa<StF16S>(&po, &co); break;
+    case SC_STORAGE_BF16: occupancy_aa<StBF16>(&po, &co); break;
+    default: occupancy_aa<StF32>(&po, &co);
+  }
+  if (po < 1 || co < 1)
+    return fail(SC_ECUDA, "the in-place step kernels cannot be made resident: %s", cudaGetErrorString(cudaGetLastError()));
+  const long long units = h->lay.aa_units;
+  h->grid = (int)std::max(1LL, std::min({(long long)sms * co, h->lay.nslots, units}));
+  h->grid_psi = (int)std::max(1LL, std::min((long long)sms * po, units));
+  h->zmax = 1;
+  h->lay.tx = kAAThreads;
+  h->lay.ty = 1;
+  return SC_OK;
+}
+
 int launch_one(sc_lbm* h, cudaStream_t st) {
+  if (h->lay.aa) {
+    cudaError_t e;
+    switch (h->p.storage) {
+      case SC_STORAGE_F16: e = launch_aa<StF16>(h, st); break;
+      case SC_STORAGE_F16_SCALED: e = launch_aa<StF16S>(h, st); break;
+      case SC_STORAGE_BF16: e = launch_aa<StBF16>(h, st); break;
+      default: e = launch_aa<StF32>(h, st);
+    }
+    if (e != cudaSuccess) return fail(SC_ECUDA, "in-place step launch failed: %s", cudaGetErrorString(e));
+    h->cur = 1 - h->cur;  // the lattice's form
+    return SC_OK;
+  }
   const int src = h->cur, dst = 1 - h->cur;
   StepArgs a{h->L, h->pop(src), h->pop(dst), h->evap(), h->lay.cols_x, h->items(), h->starts(), h->grid, st};
   cudaError_t e = step_ops(h->p.storage, h->lay.tile, h->lay.rows).launch(a);
@@ -591,7 +770,7 @@ unsigned grid_for(long long n, int threads) {
 template <class S>
 int launch_canonical(sc_lbm* h, long long s0, long long s1, float* rho, long long rs, float* f, long long fs) {
   k_canonical<S><<<grid_for(s1 - s0, 256), 256, 0, h->stream>>>(h->L, (const typename S::T*)h->pop(h->cur), s0, s1,
-                                                                  rho, rs, f, fs);
+                                                                  rho, rs, f, fs, h->odd());
   CK(cudaGetLastError());
   return SC_OK;
 }
@@ -617,6 +796,9 @@ int launch_load(sc_lbm* h, long long s0, long long s1, int mode, const float* f,
 
 int load(sc_lbm* h, long long s0, long long s1, int mode, const float* f, long long fs, const float* rho,
          long long rs, const ShapeDev& sh) {
+  // every caller loads the whole lattice; in place it is written in the even form
+  // (the two-lattice pull's slots)
+  if (h->lay.aa) h->cur = 0;
   switch (h->p.storage) {
     case SC_STORAGE_F16: return launch_load<StF16>(h, s0, s1, mode, f, fs, rho, rs, sh);
     case SC_STORAGE_F16_SCALED: return launch_load<StF16S>(h, s0, s1, mode, f, fs, rho, rs, sh);
@@ -629,7 +811,7 @@ template <class S>
 int launch_diag(sc_lbm* h) {
   dim3 grid(h->p.nz, h->lay.diag_nsplit);
   k_diag<S><<<grid, kDiagThreads, 0, h->stream>>>(h->L, (const typename S::T*)h->pop(h->cur), h->lay.diag_nsplit,
-                                                  h->diag());
+                                                  h->diag(), h->odd());
   CK(cudaGetLastError());
   return SC_OK;
 }
@@ -670,7 +852,7 @@ template <class S>
 int launch_diag_into(sc_lbm* h, double* part) {
   dim3 grid(h->p.nz, h->lay.diag_nsplit);
   k_diag<S><<<grid, kDiagThreads, 0, h->stream>>>(h->L, (const typename S::T*)h->pop(h->cur), h->lay.diag_nsplit,
-                                                  part);
+                                                  part, h->odd());
   CK(cudaGetLastError());
   return SC_OK;
 }
@@ -718,13 +900,14 @@ static int create_common(const sc_params* p, void* stream, void* buf, bool owns,
   h->base = (char*)buf;
   h->owns = owns;
   h->cur = 0;
-  LaunchCfg cfg;
-  int rc0 = plan_launch(p, h->lay, h->lay.tile, p->zchunk, &cfg);
-  if (rc0) {
-    sc_lbm_destroy(h);
-    return rc0;
+  int rc0 = SC_OK;
+  if (h->lay.aa) {
+    rc0 = plan_aa(h);
+  } else {
+    LaunchCfg cfg;
+    rc0 = plan_launch(p, h->lay, h->lay.tile, p->zchunk, &cfg);
+    if (!rc0) rc0 = apply_launch(h, cfg);
   }
-  rc0 = apply_launch(h, cfg);
   if (rc0) {
     sc_lbm_destroy(h);
     return rc0;
@@ -1043,6 +1226,11 @@ int sc_lbm_launch_info(sc_lbm* h, int32_t* tx, int32_t* ty, int32_t* zchunk, int
 
 int sc_lbm_tune(sc_lbm* h, int32_t trials, int32_t* tile, int32_t* zchunk) {
   if (!h) return fail(SC_EINVAL, "NULL handle");
+  if (h->lay.aa) {  // one configuration, and no spare buffer for trial launches
+    if (tile) *tile = 0;
+    if (zchunk) *zchunk = h->zmax;
+    return SC_OK;
+  }
   if (trials < 1) trials = 3;
   // trial launches book their evaporated mass in the read-out staging area and
   // use the handle's work-list buffer; the chosen list is uploaded at the end

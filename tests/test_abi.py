@@ -53,7 +53,7 @@ def test_direction_table_matches_oracle_order(native, oracle_mod):
                                  dict(geometry=1, sink_layers=0), dict(wall_thickness=3, wall_z0=7),
                                  dict(geometry=2, R_H=0.0), dict(tile=99), dict(G=float("nan")),
                                  dict(staging=3), dict(staging=2, nx=6), dict(zchunk=-1),
-                                 dict(staging=2, nx=12, storage="f16")])
+                                 dict(staging=2, nx=12, storage="f16"), dict(layout=2), dict(layout=-1)])
 def test_invalid_params_rejected(native, bad):
     import paper_1701_03637_gb300 as sc
     p = dict(nx=8, ny=8, nz=8)
@@ -71,3 +71,20 @@ def test_required_bytes_counts_two_lattices(native):
         assert 2 * 2 * 19 * 4 * n <= b32 < 2 * 2 * 19 * 4 * n * 1.06 + 2 ** 20
         assert 2 * 2 * 19 * 2 * n <= b16 < b32
     assert len(sc.tile_list()) >= 3
+
+
+def test_in_place_layout_holds_one_lattice(native):
+    """The in-place (AA) layout keeps one population lattice plus an FP32 (Psi^r, Psi^b)
+    array: a 1024^3 FP32 lattice fits a 284,208 MiB device that two lattices exceed."""
+    import paper_1701_03637_gb300 as sc
+    for nx, ny, nz in [(64, 64, 64), (37, 13, 11), (512, 512, 512), (1024, 1024, 1024)]:
+        n = nx * ny * nz
+        for storage, es in (("f32", 4), ("f16", 2), ("bf16", 2), ("f16s", 2)):
+            aa = sc.required_bytes(dict(nx=nx, ny=ny, nz=nz, storage=storage, layout="aa"))
+            two = sc.required_bytes(dict(nx=nx, ny=ny, nz=nz, storage=storage))
+            one = 2 * 19 * es * n + 16 * n  # populations, Psi array, FP32 density read-out area
+            assert one <= aa < one * 1.06 + 2 ** 20
+            assert two - aa >= 2 * 19 * es * n - 8 * n - 2 ** 20  # less the Psi array
+    device = 284208 * 2 ** 20
+    assert sc.required_bytes(dict(nx=1024, ny=1024, nz=1024, layout="aa")) < 0.7 * device
+    assert sc.required_bytes(dict(nx=1024, ny=1024, nz=1024)) > device

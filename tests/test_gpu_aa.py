@@ -1,0 +1,193 @@
+"""The in-place (AA) layout: the time step of Sec. II on one population lattice
+updated in place, two launches per step (Psi of every site, then stream + sink +
+force + collision). The state it reaches after any number of steps -- in either
+of its two storage forms -- is the two-lattice step's, bit for bit, for every
+storage type, geometry (walls, planar and spherical sinks) and ragged extent;
+it also matches the FP64 oracle directly, and checkpoints taken in either form
+restore into either layout."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sc():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1701_03637_gb300 as mod
+    mod.build()
+    return mod
+
+
+def _cases():
+    """Lattices of different extents, parameters and geometries (with their inits)."""
+    from paper_1701_03637_gb300.workloads import droplet, film_4x4x128
+    out = {}
+    out["film_wall_sink"] = film_4x4x128(rho_hi=0.7, rho_lo=0.04, rho_H=0.01)
+    p, i = droplet(40, 9.0, 11, spherical_sink=True)
+    p.update(nx=37, ny=33, nz=29, sphere_cx=18.0, sphere_cy=16.0, sphere_cz=14.0, R_H=12.0, G=3.4, rho_H=0.025)
+    i.update(cx=18.0, cy=16.0, cz=14.0, radius=7.0)
+    out["sphere_sink_ragged"] = (p, i)
+    p, i = droplet(32, 8.0, 5)
+    p.update(tau_r=0.9, tau_b=1.15, G=3.7)
+    out["seam_sink_unequal_tau"] = (p, i)
+    p, i = droplet(24, 6.0, 9)
+    p.update(geometry=0, nx=130, ny=17, nz=21)  # two row segments, the second ragged
+    i.update(cx=65.0, cy=8.0, cz=10.0)
+    out["periodic_two_segments"] = (p, i)
+    p, i = film_4x4x128(rho_hi=0.7, rho_lo=0.04, rho_H=0.02)
+    p.update(nx=1, ny=3, nz=12, sink_z0=11, wall_z0=5, wall_thickness=1)
+    i.update(film_z=4)
+    out["thin_column_mid_wall"] = (p, i)
+    return out
+
+
+CASES = _cases()
+
+
+def _run(sc, params, init, steps, layout):
+    lat = sc.Lattice(dict(params, layout=layout))
+    lat.init(init)
+    out = []
+    done = 0
+    for n in steps:
+        lat.step(n - done)
+        done = n
+        out.append((lat.read_populations(), lat.read_fields(), lat.diagnostics()))
+    lat.close()
+    return out
+
+
+def _same_diag(d, ref):
+    # the evaporated mass is summed in another order (per row-segment CTA instead of
+    # per tile column): equal to FP64 rounding
+    for k in ("evaporated_mass", "flux_last"):
+        assert abs(d[k] - ref[k]) <= 1e-12 * max(1.0, abs(ref[k])), (k, d[k], ref[k])
+    for k in ("mass_r", "mass_b", "interface_z", "radius", "droplet_sites", "status", "step"):
+        assert d[k] == ref[k], (k, d[k], ref[k])
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16", "f16s"])
+@pytest.mark.parametrize("case", list(CASES))
+def test_same_bits_as_two_lattices(sc, case, storage):
+    params, init = CASES[case]
+    params = dict(params, storage=storage)
+    steps = [1, 2, 7, 77, 150]  # odd and even forms; 64-step graphs replayed from both parities
+    aa = _run(sc, params, init, steps, "aa")
+    two = _run(sc, params, init, steps, "two")
+    for n, (fa, (ra, ba), da), (ft, (rt, bt), dt) in zip(steps, aa, two):
+        assert np.array_equal(fa, ft), (case, storage, n)
+        assert np.array_equal(ra, rt) and np.array_equal(ba, bt), (case, storage, n)
+        _same_diag(da, dt)
+
+
+@pytest.mark.parametrize("steps", [1, 2])
+@pytest.mark.parametrize("case", ["sphere_sink_ragged", "thin_column_mid_wall"])
+def test_random_state_matches_oracle(sc, oracle_mod, case, steps):
+    """One and two in-place steps (the two forms) of a non-equilibrium state against
+    the oracle, within 1e-6 of each population's scale as in the two-lattice tests."""
+    from paper_1701_03637_gb300.workloads import random_populations
+    params, _ = CASES[case]
+    nx, ny, nz = params["nx"], params["ny"], params["nz"]
+    _, w = sc.lattice_directions()
+    f0 = random_populations(nx, ny, nz, seed=4242 + nx, rho=(0.55, 0.25))
+    g = sc.Lattice(dict(params, layout="aa"))
+    o = oracle_mod.Lattice(params)
+    g.write_populations(f0)
+    o.set_populations(f0)
+    g.step(steps)
+    o.step(steps)
+    fg, fo = g.read_populations(), o.populations()
+    rho = np.abs(fo).sum(axis=1, keepdims=True)
+    den = np.maximum(np.maximum(np.abs(fo), w[None, :, None, None, None] * rho), 1e-30)
+    assert np.max(np.abs(fg - fo) / den) < 1e-6 * steps
+    dg, do = g.diagnostics(), o.diagnostics()
+    assert abs(dg["mass_r"] - do["mass_r"]) <= 1e-6 * abs(do["mass_r"])
+    assert abs(dg["mass_b"] - do["mass_b"]) <= 1e-6 * abs(do["mass_b"])
+    assert abs(dg["evaporated_mass"] - do["evaporated_mass"]) <= 1e-6 * max(1.0, abs(do["mass_r"]))
+    g.close()
+
+
+@pytest.mark.parametrize("case", ["sphere_sink_ragged", "film_wall_sink"])
+def test_checkpoint_from_either_form_restores_into_either_layout(sc, case):
+    params, init = CASES[case]
+    src = sc.Lattice(dict(params, layout="aa"))
+    src.init(init)
+    for taken_at in (3, 8):  # odd form, then even form
+        src.step(taken_at - src.diagnostics()["step"])
+        f = src.read_populations()
+        d = src.diagnostics()
+        results = []
+        for layout in ("aa", "two"):
+            dst = sc.Lattice(dict(params, layout=layout))
+            dst.write_populations(f)
+            dst.set_counters(d["step"], d["evaporated_mass"])
+            dst.step(5)
+            results.append((dst.read_populations(), dst.diagnostics()))
+            dst.close()
+        assert np.array_equal(results[0][0], results[1][0])
+        _same_diag(results[0][1], results[1][1])
+    src.close()
+
+
+def test_init_returns_to_the_even_form(sc):
+    params, init = CASES["seam_sink_unequal_tau"]
+    a = sc.Lattice(dict(params, layout="aa"))
+    a.init(init)
+    a.step(3)  # odd form
+    a.init(init)
+    a.step(4)
+    b = sc.Lattice(dict(params, layout="aa"))
+    b.init(init)
+    b.step(4)
+    assert np.array_equal(a.read_populations(), b.read_populations())
+    assert a.diagnostics()["step"] == b.diagnostics()["step"] == 4
+    a.close()
+    b.close()
+
+
+def test_launch_info_and_tuner_report_the_in_place_step(sc):
+    params, init = CASES["periodic_two_segments"]
+    lat = sc.Lattice(dict(params, layout="aa"))
+    lat.init(init)
+    info = lat.launch_info()
+    assert info["tile_y"] == 1 and info["zchunk"] == 1 and info["staging"] == "thread"
+    assert info["tile_x"] == 128 and 1 <= info["ctas"] <= 2 * 17 * 21  # row segments of the lattice
+    before = lat.read_populations()
+    assert lat.tune() == dict(tile=0, zchunk=1)
+    assert np.array_equal(lat.read_populations(), before)
+    lat.close()
+
+
+def test_batch_rejects_in_place_members(sc):
+    params, _ = CASES["seam_sink_unequal_tau"]
+    b = sc.Batch(1 << 28)
+    with pytest.raises(sc.ScError, match="-1"):
+        b.add(dict(params, layout="aa"))
+    b.close()
+
+
+@pytest.mark.parametrize("n", [128, 256])
+def test_full_size_droplet_same_bits(sc, n):
+    """The benchmark's droplet (planar sinks across the z seam) at 128^3 and 256^3:
+    densities equal to the two-lattice step's after an odd and an even number of
+    steps, compared on the device."""
+    import torch
+    from paper_1701_03637_gb300.workloads import droplet
+    params, init = droplet(n, 24.0 * n / 128, 1)
+    fields = {}
+    for layout in ("aa", "two"):
+        lat = sc.Lattice(dict(params, layout=layout))
+        lat.init(init)
+        lat.step(9)
+        f9 = lat.read_fields_device().clone()
+        lat.step(11)
+        f20 = lat.read_fields_device().clone()
+        fields[layout] = (f9, f20, lat.diagnostics())
+        lat.close()
+        torch.cuda.synchronize()
+    for k in (0, 1):
+        assert torch.equal(fields["aa"][k], fields["two"][k]), k
+    _same_diag(fields["aa"][2], fields["two"][2])
