@@ -1,7 +1,9 @@
 #!/usr/bin/env python
 """Benchmark of the fused two-component Shan-Chen D3Q19 evaporation step.
 
-One benchmark step = one lattice time step (one fused launch) of the workload.
+One benchmark step = one lattice time step of the workload: one fused launch
+with two population lattices, two launches with one lattice updated in place
+(--layout aa).
 Default workload: the 128^3 floating droplet (radius 24, centred; sinks at the
 z-boundary planes z = 127 and z = 0; tau = 1, G = 3.6, rho_H = 0.03; FP32
 populations, two-lattice pull layout; seeded +-1e-4 noise). Its populations
@@ -31,6 +33,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 BYTES_PER_SITE = {"f32": 304, "f16": 152, "bf16": 152, "f16s": 152}  # read + write 2 x 19 populations
+# bytes the in-place (AA) step moves per site: its Psi pass reads the 2 x 19
+# populations and writes (Psi^r, Psi^b) in FP32, its collision reads them again
+# with Psi and writes them back
+AA_BYTES_PER_SITE = {k: 3 * v // 2 + 16 for k, v in BYTES_PER_SITE.items()}
 PROFILE_FILE = os.path.join(ROOT, "profiles", "k_step_droplet_128.md")
 
 
@@ -44,6 +50,8 @@ def parse():
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16", "f16s"])
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--zchunk", type=int, default=0)
+    ap.add_argument("--layout", default="two", choices=["two", "aa"],
+                    help="two population lattices, or one updated in place (half the memory)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the automatic kernel configuration")
@@ -52,10 +60,10 @@ def parse():
     return ap.parse_args()
 
 
-def workload(name, storage, tile=0, zchunk=0):
+def workload(name, storage, tile=0, zchunk=0, layout="two"):
     from paper_1701_03637_gb300.workloads import WORKLOADS
     params, init = WORKLOADS[name](storage=storage)
-    params.update(tile=tile, zchunk=zchunk)
+    params.update(tile=tile, zchunk=zchunk, layout=layout)
     return params, init
 
 
@@ -64,7 +72,9 @@ def describe(name, params, storage):
     geom = {0: "periodic", 1: f"planar sink z={params.get('sink_z0')} x{params.get('sink_layers')} layers",
             2: f"spherical sink R_H={params.get('R_H')}"}[params.get("geometry", 0)]
     return (f"{name}: {params['nx']}x{params['ny']}x{params['nz']} two-component D3Q19 Shan-Chen droplet, "
-            f"{geom}, tau=1, G=3.6, rho_H={params['rho_H']}, {storage} populations, two-lattice pull")
+            f"{geom}, tau=1, G=3.6, rho_H={params['rho_H']}, {storage} populations, "
+            + ("one lattice in place (AA: Psi pass + collision)" if params.get("layout") == "aa"
+               else "two-lattice pull"))
 
 
 def source_digest():
@@ -268,12 +278,13 @@ def run_ours(args):
     def slowest(v):
         return max_over_ranks(v, world, "cuda")
 
-    params, init = workload(args.workload, args.storage, args.tile, args.zchunk)
+    params, init = workload(args.workload, args.storage, args.tile, args.zchunk, args.layout)
     n = params["nx"] * params["ny"] * params["nz"]
+    aa = args.layout == "aa"
     lat = sc.Lattice(params)
     lat.init(init)
     tuned = None
-    if not args.tile and not args.zchunk and not args.no_tune:
+    if not args.tile and not args.zchunk and not args.no_tune and not aa:
         tuned = lat.tune(trials=5)  # untimed; leaves the state unchanged
     stream = torch.cuda.current_stream()
     lat.step(args.warmup)
@@ -307,9 +318,15 @@ def run_ours(args):
     peak, peak_kind = measured_peak_hbm()
     achieved = BYTES_PER_SITE[args.storage] * n / step_s / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": profiled_traffic(args.workload, args.storage, *launch_cfg(lat)),
+            "traffic": None if aa else profiled_traffic(args.workload, args.storage, *launch_cfg(lat)),
             "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
             "algorithmic_bytes_per_site": BYTES_PER_SITE[args.storage]}
+    if aa:
+        # both launches of the step together, against the method's algorithmic bytes;
+        # the bytes the two launches move are reported beside them
+        roof.update(kernel="k_aa_psi + k_aa_collide (one step)",
+                    implementation_bytes_per_site=AA_BYTES_PER_SITE[args.storage],
+                    implementation_frac=AA_BYTES_PER_SITE[args.storage] * n / step_s / 1e9 / peak)
 
     # end to end through the public API: initial densities from pinned host memory,
     # the steps with FP64 diagnostics read back every 100 steps, final densities to host
@@ -363,9 +380,9 @@ def run_ours(args):
                "config": {"workload": describe(args.workload, params, args.storage),
                           "sites": n, "lattices_per_gpu": 1, "l2": "inputs larger than L2 (no flush)",
                           "tile": f"{info['tile_x']}x{info['tile_y']}", "zchunk": info["zchunk"],
-                          "ctas": info["ctas"], "staging": info["staging"],
+                          "ctas": info["ctas"], "staging": info["staging"], "layout": args.layout,
                           "autotuned": tuned is not None, "parallelism": f"independent replicas x{world}"},
-               "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
+               "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": (2 if aa else 1) * args.steps,
                "clocks": clk, "diag": {k: d[k] for k in ("mass_r", "mass_b", "evaporated_mass", "radius")}}
         print(json.dumps(out))
     lat.close()
