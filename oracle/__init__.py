@@ -45,7 +45,8 @@ class Params(C.Structure):
                 ("tau_r", C.c_double), ("tau_b", C.c_double), ("G", C.c_double), ("rho_H", C.c_double),
                 ("geometry", C.c_int32), ("sink_z0", C.c_int32), ("sink_layers", C.c_int32),
                 ("sphere_cx", C.c_double), ("sphere_cy", C.c_double), ("sphere_cz", C.c_double),
-                ("R_H", C.c_double), ("wall_z0", C.c_int32), ("wall_thickness", C.c_int32)]
+                ("R_H", C.c_double), ("wall_z0", C.c_int32), ("wall_thickness", C.c_int32),
+                ("G_rr", C.c_double), ("G_bb", C.c_double)]
 
 
 class Init(C.Structure):
@@ -124,7 +125,8 @@ def uniform(seed: int, k: int) -> float:
 
 
 _PARAM_DEFAULTS = dict(tau_r=1.0, tau_b=1.0, G=3.6, rho_H=0.03, geometry=0, sink_z0=0, sink_layers=1,
-                       sphere_cx=0.0, sphere_cy=0.0, sphere_cz=0.0, R_H=0.0, wall_z0=0, wall_thickness=0)
+                       sphere_cx=0.0, sphere_cy=0.0, sphere_cz=0.0, R_H=0.0, wall_z0=0, wall_thickness=0,
+                       G_rr=0.0, G_bb=0.0)
 _INIT_DEFAULTS = dict(shape=0, film_z=0, cx=0.0, cy=0.0, cz=0.0, radius=0.0, rho_hi=1.0, rho_lo=0.03,
                       noise_amp=0.0, seed=0)
 

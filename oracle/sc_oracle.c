@@ -5,7 +5,10 @@
  *
  *   densities       rho^c = sum_i f_i^c                        (Sec. II A, after Eq. 2)
  *   pseudopotential Psi(rho) = 1 - exp(-rho/rho0), rho0 = 1    (Eq. 4)
- *   force           F^c = -Psi^c(x) g sum_i w_i Psi^cbar(x+e_i) e_i   (Eq. 3)
+ *   force           F^c = -Psi^c(x) sum_cbar g^{c cbar} sum_i w_i Psi^cbar(x+e_i) e_i   (Eq. 3),
+ *                   the sum over cbar in {r, b} with g^{rb} = g^{br} = G and the self
+ *                   couplings g^{rr}, g^{bb} (0 in the paper's runs; g^{cc} < 0 is the
+ *                   multiphase pseudopotential model the paper names as an extension)
  *   common velocity u' = sum_c (m^c/tau_c) / sum_c (rho^c/tau_c) (reduces to the
  *                   paper's mass-weighted u_eq when tau_r = tau_b)   (Sec. II A)
  *   shifted velocity u^c_eq = u' + tau_c F^c / rho^c             (Sec. II B)
@@ -223,6 +226,32 @@ static void densities(orc_lattice* L) {
   }
 }
 
+/* Eq. (3) at fluid site (x, y, z) from the current Psi: for each component c,
+   F^c = -Psi^c(x) sum_cbar g^{c cbar} sum_{i>=1} w_i Psi^cbar(x + e_i) e_i, periodic
+   neighbours (solid ones have Psi = 0). The cross term is evaluated first, as
+   -Psi^c(x) G a^cbar; the self term -Psi^c(x) g^{cc} a^c is added to it. */
+static void force(const orc_lattice* L, int x, int y, int z, double Fc[2][3]) {
+  const orc_params* p = &L->p;
+  const int64_t n = L->n;
+  const int nx = p->nx, ny = p->ny, nz = p->nz;
+  const int64_t s = x + (int64_t)nx * (y + (int64_t)ny * z);
+  const double gself[2] = {p->G_rr, p->G_bb};
+  double a[2][3] = {{0, 0, 0}, {0, 0, 0}};  /* a^cbar = sum_i w_i Psi^cbar(x + e_i) e_i */
+  for (int cb = 0; cb < 2; ++cb)
+    for (int i = 1; i < Q; ++i) {
+      int64_t xn = wrapi(x + CX[i], nx), yn = wrapi(y + CY[i], ny), zn = wrapi(z + CZ[i], nz);
+      double pn = L->psi[cb * n + xn + (int64_t)nx * (yn + (int64_t)ny * zn)];
+      a[cb][0] += W[i] * pn * CX[i];
+      a[cb][1] += W[i] * pn * CY[i];
+      a[cb][2] += W[i] * pn * CZ[i];
+    }
+  for (int c = 0; c < 2; ++c)
+    for (int d = 0; d < 3; ++d) {
+      Fc[c][d] = -L->psi[c * n + s] * p->G * a[1 - c][d];
+      if (gself[c] != 0.0) Fc[c][d] += -L->psi[c * n + s] * gself[c] * a[c][d];
+    }
+}
+
 static void one_step(orc_lattice* L) {
   const orc_params* p = &L->p;
   const int64_t n = L->n;
@@ -241,19 +270,8 @@ static void one_step(orc_lattice* L) {
             for (int i = 0; i < Q; ++i) L->ftmp[((int64_t)c * Q + i) * n + s] = F(L, c, i, s);
           continue;
         }
-        double Fc[2][3] = {{0, 0, 0}, {0, 0, 0}};
-        for (int c = 0; c < 2; ++c) {
-          const int cb = 1 - c;
-          double acc[3] = {0, 0, 0};
-          for (int i = 1; i < Q; ++i) {
-            int64_t xn = wrapi(x + CX[i], nx), yn = wrapi(y + CY[i], ny), zn = wrapi(z + CZ[i], nz);
-            double pn = L->psi[cb * n + xn + (int64_t)nx * (yn + (int64_t)ny * zn)];
-            acc[0] += W[i] * pn * CX[i];
-            acc[1] += W[i] * pn * CY[i];
-            acc[2] += W[i] * pn * CZ[i];
-          }
-          for (int d = 0; d < 3; ++d) Fc[c][d] = -L->psi[c * n + s] * p->G * acc[d]; /* Eq. (3) */
-        }
+        double Fc[2][3];
+        force(L, x, y, z, Fc);
         double m[2][3] = {{0, 0, 0}, {0, 0, 0}};
         for (int c = 0; c < 2; ++c)
           for (int i = 0; i < Q; ++i) {
@@ -380,14 +398,8 @@ void orc_flux_field(const orc_lattice* L, double* j) {
         const int64_t s = x + (int64_t)nx * (y + (int64_t)ny * z);
         if (L->cls[s] != 0) { j[s] = j[n + s] = j[2 * n + s] = 0.0; continue; }
         double Fc[2][3], m[2][3] = {{0, 0, 0}, {0, 0, 0}};
+        force(L, x, y, z, Fc);
         for (int c = 0; c < 2; ++c) {
-          double acc[3] = {0, 0, 0};
-          for (int i = 1; i < Q; ++i) {
-            int64_t xn = wrapi(x + CX[i], nx), yn = wrapi(y + CY[i], ny), zn = wrapi(z + CZ[i], nz);
-            double pn = L->psi[(1 - c) * n + xn + (int64_t)nx * (yn + (int64_t)ny * zn)];
-            acc[0] += W[i] * pn * CX[i]; acc[1] += W[i] * pn * CY[i]; acc[2] += W[i] * pn * CZ[i];
-          }
-          for (int d = 0; d < 3; ++d) Fc[c][d] = -L->psi[c * n + s] * p->G * acc[d];
           for (int i = 0; i < Q; ++i) {
             double fi = F(L, c, i, s);
             m[c][0] += fi * CX[i]; m[c][1] += fi * CY[i]; m[c][2] += fi * CZ[i];

@@ -28,6 +28,7 @@ typedef struct orc_params {
   int32_t sink_z0, sink_layers;
   double sphere_cx, sphere_cy, sphere_cz, R_H;
   int32_t wall_z0, wall_thickness;   /* solid slab z in [wall_z0, wall_z0+thickness) */
+  double G_rr, G_bb;         /* self couplings g^{rr}, g^{bb} of Eq. (3) (0 in all of the paper's runs) */
 } orc_params;
 
 typedef struct orc_init {

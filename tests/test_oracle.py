@@ -322,3 +322,82 @@ def test_film_evaporation_flux_law(oracle_mod):
         assert abs(d["flux_last"] / 16 / j_th - 1) < 0.08
         assert d["interface_z"] < d0["interface_z"]
         assert abs((d["mass_r"] + d["evaporated_mass"]) - (d0["mass_r"] + d0["evaporated_mass"])) < 1e-9
+
+
+def test_total_momentum_conserved_with_self_couplings(oracle_mod):
+    """With the self couplings of Eq. (3) (sum over cbar including c) the force still
+    vanishes pairwise over a periodic lattice, so total momentum stays exact. Unequal
+    g^{rr} and g^{bb} make a self term built from the wrong component's Psi break it."""
+    nx, ny, nz = 6, 5, 7
+    L = oracle_mod.Lattice(dict(nx=nx, ny=ny, nz=nz, G=2.0, G_rr=-1.3, G_bb=0.6, tau_r=1.0, tau_b=0.9))
+    L.set_populations(_random_state(nx, ny, nz, 14))
+    c, _, _ = oracle_mod.tables()
+
+    def mom():
+        return np.einsum("cin,ia->a", L.populations().reshape(2, Q, -1), c.astype(np.float64))
+
+    p0 = mom()
+    L.step(30)
+    assert np.allclose(mom(), p0, atol=1e-13)
+
+
+def _sc_coexistence(g):
+    """Coexistence densities of the single-component pseudopotential fluid with
+    Psi = 1 - exp(-rho) (Eq. (4)) and p = c_s^2 rho + (g c_s^2 / 2) Psi^2 (the
+    self-coupling force of Eq. (3) expanded to second order): p(rho_g) = p(rho_l) = p0
+    and the integral of (p0 - p) Psi' / Psi^2 from rho_g to rho_l vanishes (Shan and
+    Chen's mechanical-stability condition, which replaces Maxwell's equal areas for
+    this force)."""
+    from scipy import integrate, optimize
+    cs2 = 1.0 / 3.0
+
+    def psi(r):
+        return -np.expm1(-r)
+
+    def p(r):
+        return cs2 * r + 0.5 * g * cs2 * psi(r) ** 2
+
+    def eqs(v):
+        rg, rl = v
+        p0 = p(rg)
+        area = integrate.quad(lambda r: (p0 - p(r)) * np.exp(-r) / psi(r) ** 2, rg, rl, epsabs=1e-13)[0]
+        return [p(rl) - p0, area]
+
+    return optimize.fsolve(eqs, [0.1, 2.0], xtol=1e-13)
+
+
+@pytest.mark.parametrize("g", [-4.5, -5.0, -6.0])
+def test_single_component_coexistence_matches_mechanical_stability(oracle_mod, g):
+    """The multiphase pseudopotential model the paper names as an extension: component
+    b absent, g^{rr} = g below the critical -4 (Psi = 1/2, rho = ln 2). A flat liquid
+    slab in a periodic 1 x 1 x 80 column settles to the coexistence densities of the
+    mechanical-stability condition (the lattice adds under 1%); b stays exactly zero."""
+    rg, rl = _sc_coexistence(g)
+    assert rg < np.log(2.0) < rl
+    nz = 80
+    z = np.arange(nz)
+    rho = np.where((z >= 20) & (z < 60), rl, rg).reshape(nz, 1, 1).astype(np.float64)
+    L = oracle_mod.Lattice(dict(nx=1, ny=1, nz=nz, G=0.0, G_rr=g, G_bb=0.0))
+    L.init_fields(rho, np.zeros_like(rho))
+    L.step(10000)
+    rr, rb = L.fields()
+    assert abs(rr[40, 0, 0] / rl - 1.0) < 2e-3
+    assert abs(rr[0, 0, 0] / rg - 1.0) < 1e-2
+    assert np.all(rb == 0.0)
+
+
+def test_self_coupling_separates_phases_inside_the_spinodal(oracle_mod):
+    """A 1% density wave about rho = ln 2 (inside the spinodal for g < -4) grows to the
+    coexistence densities with g^{rr} = -5 and decays without self coupling."""
+    nz = 64
+    z = np.arange(nz)
+    rho = (np.log(2.0) * (1.0 + 0.01 * np.cos(2 * np.pi * z / nz))).reshape(nz, 1, 1)
+    rg, rl = _sc_coexistence(-5.0)
+    out = {}
+    for g in (-5.0, 0.0):
+        L = oracle_mod.Lattice(dict(nx=1, ny=1, nz=nz, G=0.0, G_rr=g))
+        L.init_fields(rho, np.zeros_like(rho))
+        L.step(10000)
+        out[g] = L.fields()[0]
+    assert abs(out[-5.0].max() / rl - 1.0) < 5e-3 and abs(out[-5.0].min() / rg - 1.0) < 2e-2
+    assert out[0.0].max() - out[0.0].min() < 1e-3 * np.log(2.0)
