@@ -62,12 +62,13 @@ def surface_tension(radii=(8.0, 12.0, 16.0), margin=12, steps=4000, G=3.6, tau=1
 
 
 def evaporating_droplet(n, R0, rho_H=0.01, G=3.6, tau=1.0, rho=(0.7, 0.04), equilibrate=2000, steps=20000,
-                        every=500, R_H=None, R_stop=4.0, seed=5, storage="f32"):
+                        every=500, R_H=None, R_stop=4.0, seed=5, storage="f32", tune=False):
     """A droplet equilibrates with the sink closed, then evaporates through the
     spherical sink r >= R_H (default n/2 - 2) with rho^r = rho_H there. Returns
     the radius series R(t) (t counted from opening the sink), the coexistence
     densities at the start (rho^r at the centre, the r vapour density in the
-    shell R + 4 < r < R + 6, rho^b far outside) and R_H."""
+    shell R + 4 < r < R + 6, rho^b far outside) and R_H. tune: let the step's
+    autotuner pick the kernel configuration of the evaporation run (same bits)."""
     R_H = n / 2.0 - 2.0 if R_H is None else R_H
     eq = Lattice(_droplet_params(n, G, tau, storage=storage))
     eq.init(_init(n, R0, rho, seed))
@@ -84,6 +85,8 @@ def evaporating_droplet(n, R0, rho_H=0.01, G=3.6, tau=1.0, rho=(0.7, 0.04), equi
     rho_b_out = float(rb[0, 0, 0])
     ev = Lattice(_droplet_params(n, G, tau, geometry=2, R_H=R_H, rho_H=rho_H, storage=storage))
     ev.write_populations(f)
+    if tune:
+        ev.tune()
     ts, Rs, fluxes = [0], [R_start], [0.0]
     done = 0
     while done < steps:

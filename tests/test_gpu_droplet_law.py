@@ -30,24 +30,8 @@ def sc():
     return mod
 
 
-def _law_dR(A, R_start, T, R0, gamma, run, d0=2.5, dt=10.0):
-    def rhs(R):
-        _, mi = A.laplace_densities(R, R0, gamma, run["rho_ma0"], run["rho_mi0"])
-        D = float(A.diffusion_coefficient(mi, run["rho_b_out"], run["G"]))
-        return A.drop_mass_rate(R, run["R_H"], d0, D, mi, run["rho_H"]) / A._dMdR(
-            R, run["R_H"], d0, run["rho_ma0"], run["rho_mi0"], run["rho_H"], R0=R0, gamma=gamma)
-
-    R = R_start
-    for _ in range(int(round(T / dt))):
-        k1 = rhs(R)
-        k2 = rhs(R + 0.5 * dt * k1)
-        k3 = rhs(R + 0.5 * dt * k2)
-        k4 = rhs(R + dt * k3)
-        R += dt / 6.0 * (k1 + 2 * k2 + 2 * k3 + k4)
-    return R - R_start
-
-
 def test_droplet_radius_follows_the_laplace_corrected_law(sc):
+    from tests.droplet_law import law_dR as _law_dR
     from oracle import analytic as A
     from paper_1701_03637_gb300 import experiments as X
     lap = X.surface_tension(radii=(8.0, 12.0, 16.0), steps=4000)

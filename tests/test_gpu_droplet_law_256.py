@@ -1,0 +1,73 @@
+"""The evaporating droplet of Sec. III C at the paper's own scale: a droplet of
+radius 65 (densities 0.70 / 0.04) in a 256^3 box, equilibrated with the sink
+closed, then evaporating through the spherical sink r >= R_H = 126 with
+rho_H = 0.02 and 0.03 (two of the paper's three values). Over the window after
+the diffusive set-up time (R_H - R)^2 / D ~ 3e4 steps its radius must shrink as
+the Laplace-corrected law Eq. (drop-r-df4) integrated from the measured state
+predicts (surface tension from a Laplace test; coexistence densities and the
+vapour D^c of Sec. III A measured on the run; d0 = 2.5).
+
+About ten minutes of GPU time, so it runs only when SC_PAPER_SCALE=1:
+
+    SC_PAPER_SCALE=1 python -m pytest tests/test_gpu_droplet_law_256.py -q
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(os.environ.get("SC_PAPER_SCALE") != "1",
+                                 reason="paper-scale run (about ten GPU minutes): set SC_PAPER_SCALE=1")]
+
+OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "..", "gpurun_out")
+STEPS = 250000
+WINDOW = (50000.0, 250000.0)
+
+
+@pytest.fixture(scope="module")
+def sc():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1701_03637_gb300 as mod
+    mod.build()
+    return mod
+
+
+@pytest.fixture(scope="module")
+def gamma(sc):
+    from paper_1701_03637_gb300 import experiments as X
+    lap = X.surface_tension(radii=(8.0, 12.0, 16.0), steps=4000, rho=(0.70, 0.04))
+    assert lap["gamma"] > 0
+    return lap["gamma"]
+
+
+@pytest.mark.parametrize("rho_H", [0.02, 0.03])
+def test_paper_scale_droplet_follows_the_law(sc, gamma, rho_H):
+    from oracle import analytic as A
+    from paper_1701_03637_gb300 import experiments as X
+    from tests.droplet_law import law_dR
+    run = X.evaporating_droplet(256, 65.0, rho_H=rho_H, rho=(0.70, 0.04), equilibrate=4000, steps=STEPS,
+                                every=5000, tune=True)
+    t, R = run["t"], run["R"]
+    R0 = float(R[0])
+    t0, t1 = WINDOW
+    R_t0 = float(np.interp(t0, t, R))
+    sim = float(np.interp(t1, t, R)) - R_t0
+    law = law_dR(A, R_t0, t1 - t0, R0, gamma, run, dt=50.0)
+    law0 = law_dR(A, R_t0, t1 - t0, R0, 0.0, run, dt=50.0)
+    rec = dict(rho_H=rho_H, gamma=gamma, R0=R0, R_t0=R_t0, window=WINDOW, dR_sim=sim, dR_law=law,
+               dR_law_no_laplace=law0, rho_ma0=run["rho_ma0"], rho_mi0=run["rho_mi0"],
+               rho_b_out=run["rho_b_out"], R_H=run["R_H"], t=t.tolist(), R=R.tolist(),
+               evaporated_mass=run["evaporated_mass"].tolist())
+    try:
+        os.makedirs(OUT, exist_ok=True)
+        with open(os.path.join(OUT, f"droplet_law_256_{rho_H}.json"), "w") as fh:
+            json.dump(rec, fh, indent=1)
+    except OSError:
+        pass
+    print(json.dumps({k: v for k, v in rec.items() if k not in ("t", "R", "evaporated_mass")}))
+    assert sim < 0
+    assert abs(sim - law) < 0.10 * abs(law), (sim, law, law0)
