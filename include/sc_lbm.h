@@ -9,7 +9,8 @@
  *     equilibrium of Eq. (2) with c_s^2 = 1/3, weights 1/3, 1/18, 1/36;
  *   - densities rho^c = sum_i f_i^c, pseudopotential Psi = 1 - exp(-rho), Eq. (4);
  *   - inter-component force F^c = -Psi^c(x) g sum_i w_i Psi^cbar(x + e_i) e_i, Eq. (3),
- *     applied as the velocity shift tau F^c / rho^c on the common velocity;
+ *     applied as the velocity shift tau F^c / rho^c on the common velocity (with
+ *     optional self couplings g^{cc}: the same sum over cbar = c);
  *   - periodic boundaries, halfway bounce-back at solid sites (Sec. II A);
  *   - evaporation sink (Sec. II C): at sink sites the evaporating component r is
  *     reset to f_i = w_i rho_H and the other component b to
@@ -101,6 +102,13 @@ typedef struct sc_params {
   int32_t zchunk;                 /* planes per CTA along z: 0 = automatic */
   int32_t staging;                /* SC_STAGING_*: how the step kernel gathers its pulls */
   int32_t layout;                 /* SC_LAYOUT_*: two lattices or one updated in place */
+  double G_rr, G_bb;              /* self couplings g^{rr}, g^{bb}: Eq. (3) sums the force over every
+                                     component cbar, cbar = c included; the paper's runs have
+                                     only g^{rb} = g^{br} = G (self couplings 0). g^{cc} < -4
+                                     separates component c into liquid and vapour on its own
+                                     (the multiphase pseudopotential model the paper names as an
+                                     extension; with rho^b = 0 everywhere, the single-component
+                                     model). Finite. */
 } sc_params;
 
 /* Seeded initial state: film or droplet with uniform noise. */

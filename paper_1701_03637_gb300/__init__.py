@@ -23,7 +23,7 @@ __all__ = ["Lattice", "Batch", "ScError", "build", "lattice_directions", "tile_l
 
 _PARAM_DEFAULTS = dict(tau_r=1.0, tau_b=1.0, G=3.6, rho_H=0.03, geometry=0, sink_z0=0, sink_layers=1,
                        sphere_cx=0.0, sphere_cy=0.0, sphere_cz=0.0, R_H=0.0, wall_z0=0, wall_thickness=0,
-                       storage=0, tile=0, zchunk=0, staging=0, layout=0)
+                       storage=0, tile=0, zchunk=0, staging=0, layout=0, G_rr=0.0, G_bb=0.0)
 _INIT_DEFAULTS = dict(shape=0, film_z=0, cx=0.0, cy=0.0, cz=0.0, radius=0.0, rho_hi=1.0, rho_lo=0.03,
                       noise_amp=0.0, seed=0)
 

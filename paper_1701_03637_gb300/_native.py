@@ -66,7 +66,7 @@ class Params(C.Structure):
                 ("sphere_cx", C.c_double), ("sphere_cy", C.c_double), ("sphere_cz", C.c_double),
                 ("R_H", C.c_double), ("wall_z0", C.c_int32), ("wall_thickness", C.c_int32),
                 ("storage", C.c_int32), ("tile", C.c_int32), ("zchunk", C.c_int32),
-                ("staging", C.c_int32), ("layout", C.c_int32)]
+                ("staging", C.c_int32), ("layout", C.c_int32), ("G_rr", C.c_double), ("G_bb", C.c_double)]
 
 
 class Init(C.Structure):

@@ -67,6 +67,7 @@ struct LatDev {
   long long np;            // elements between consecutive (component, direction) arrays
   float omega[2], tau[2];  // 1/tau and tau per component
   float G, rhoH;           // g of Eq. (3); imposed rho^r at sinks
+  float Gs[2];             // self couplings g^{rr}, g^{bb} of Eq. (3) (0: the paper's two-component model)
   double rhoH_mass;        // exact sum of the reset r populations fl(w_i rho_H)
   int geometry, sink_z0, sink_layers;  // sink_z0 in [0, nz)
   double scx, scy, scz, RH2;
@@ -364,17 +365,19 @@ __device__ __forceinline__ float cdot(const float (&u)[3]) {
 }
 
 // Shifted-velocity BGK relaxation of component c at a fluid site (Eqs. (1)-(3)):
-// u_eq = u' + tau_c F^c / rho^c with F^c = -g Psi^c(x) a, a = sum_i w_i Psi^cbar(x + e_i) e_i.
-__device__ __forceinline__ void relax(const LatDev& L, int c, float (&f)[Q], float rho, float ps,
-                                      const float (&a)[3], const float (&up)[3]) {
+// u_eq = u' + tau_c F^c / rho^c with F^c = -Psi^c(x) g A: g = G and A = a^cbar =
+// sum_i w_i Psi^cbar(x + e_i) e_i in the paper's two-component model, g = 1 and
+// A = sum_cbar g^{c cbar} a^cbar (coupled_sums) with self couplings.
+__device__ __forceinline__ void relax(const LatDev& L, int c, float (&f)[Q], float rho, float ps, float g,
+                                      const float (&A)[3], const float (&up)[3]) {
   const float om = c == 0 ? L.omega[0] : L.omega[1], tau = c == 0 ? L.tau[0] : L.tau[1];
-  // tau F / rho = (-g tau) (Psi / rho) a with Psi / rho <= 1, so a trace (or
+  // tau F / rho = (-g tau) (Psi / rho) A with Psi / rho <= 1, so a trace (or
   // denormal) density cannot overflow the shift; rho = 0 takes u' itself
   const float q = rho > 0.0f ? __fdiv_rn(ps, rho) : 0.0f;
-  const float gq = __fmul_rn(__fmul_rn(-L.G, tau), q);
+  const float gq = __fmul_rn(__fmul_rn(-g, tau), q);
   float u[3];
 #pragma unroll
-  for (int d = 0; d < 3; ++d) u[d] = __fmaf_rn(gq, a[d], up[d]);
+  for (int d = 0; d < 3; ++d) u[d] = __fmaf_rn(gq, A[d], up[d]);
   const float usq = __fmaf_rn(u[0], u[0], __fmaf_rn(u[1], u[1], __fmul_rn(u[2], u[2])));
   const float base = __fmaf_rn(-1.5f, usq, 1.0f);  // 1 - 1.5 u.u
   // f^eq_i = w_i rho (1 + 3 c.u + 4.5 (c.u)^2 - 1.5 u.u); opposite directions share
@@ -396,6 +399,18 @@ __device__ __forceinline__ void relax(const LatDev& L, int c, float (&f)[Q], flo
   });
 }
 
+// A^c = sum_cbar g^{c cbar} a^cbar of Eq. (3): the cross coupling g (= g^{rb} = g^{br})
+// times the other component's sum, plus the self coupling g^{cc} times its own
+// (an exact zero when g^{cc} = 0, the paper's two-component model).
+__device__ __forceinline__ void coupled_sums(const LatDev& L, const float (&ar)[3], const float (&ab)[3],
+                                             float (&Ar)[3], float (&Ab)[3]) {
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    Ar[d] = __fmaf_rn(L.Gs[0], ar[d], __fmul_rn(L.G, ab[d]));
+    Ab[d] = __fmaf_rn(L.Gs[1], ab[d], __fmul_rn(L.G, ar[d]));
+  }
+}
+
 // Shifted-velocity BGK collision of one fluid site, in place on fr/fb.
 // ar/ab: sum_i w_i Psi^{r|b}(x + e_i) e_i.
 __device__ __forceinline__ void collide(const LatDev& L, float (&fr)[Q], float (&fb)[Q], float rr, float rb, float psr,
@@ -404,8 +419,15 @@ __device__ __forceinline__ void collide(const LatDev& L, float (&fr)[Q], float (
   momentum(fr, mr);
   momentum(fb, mb);
   common_velocity(L, rr, rb, mr, mb, up);
-  relax(L, 0, fr, rr, psr, ab, up);
-  relax(L, 1, fb, rb, psb, ar, up);
+  if (L.Gs[0] == 0.0f && L.Gs[1] == 0.0f) {  // the paper's model: the cross coupling alone
+    relax(L, 0, fr, rr, psr, L.G, ab, up);
+    relax(L, 1, fb, rb, psb, L.G, ar, up);
+  } else {
+    float Ar[3], Ab[3];
+    coupled_sums(L, ar, ab, Ar, Ab);
+    relax(L, 0, fr, rr, psr, 1.0f, Ar, up);
+    relax(L, 1, fb, rb, psb, 1.0f, Ab, up);
+  }
 }
 
 // sum_i w_i Psi^c(x + e_i) e_i of both components from a Psi ring whose cells hold

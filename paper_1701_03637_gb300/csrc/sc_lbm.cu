@@ -549,6 +549,7 @@ int validate(const sc_params* p) {
   if (!(p->tau_r > 0.5) || !(p->tau_b > 0.5) || !std::isfinite(p->tau_r) || !std::isfinite(p->tau_b))
     return fail(SC_EINVAL, "tau must exceed 1/2");
   if (!std::isfinite(p->G) || !std::isfinite(p->rho_H)) return fail(SC_EINVAL, "G and rho_H must be finite");
+  if (!std::isfinite(p->G_rr) || !std::isfinite(p->G_bb)) return fail(SC_EINVAL, "self couplings must be finite");
   if (p->geometry < 0 || p->geometry > 2) return fail(SC_EINVAL, "unknown geometry %d", p->geometry);
   if (p->geometry == 1 && (p->sink_layers < 1 || p->sink_layers > p->nz))
     return fail(SC_EINVAL, "sink_layers must be in [1, nz]");
@@ -576,6 +577,8 @@ LatDev make_dev(const sc_params* p, const Layout& l) {
   L.tau[0] = (float)p->tau_r; L.tau[1] = (float)p->tau_b;
   L.omega[0] = (float)(1.0 / p->tau_r); L.omega[1] = (float)(1.0 / p->tau_b);
   L.G = (float)p->G;
+  L.Gs[0] = (float)p->G_rr;
+  L.Gs[1] = (float)p->G_bb;
   L.rhoH = (float)p->rho_H;
   L.rhoH_mass = 0.0;
   for (int i = 0; i < Q; ++i) L.rhoH_mass += (double)(wgt(i) * (float)p->rho_H);

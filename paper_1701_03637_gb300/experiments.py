@@ -18,13 +18,14 @@ from . import Lattice
 CS2 = 1.0 / 3.0
 
 
-def bulk_pressure(rho_r, rho_b, G):
+def bulk_pressure(rho_r, rho_b, G, G_rr=0.0, G_bb=0.0):
     """Bulk pressure of the two-component Shan-Chen fluid with Psi = 1 - exp(-rho):
     c_s^2 (rho^r + rho^b) + G c_s^2 Psi^r Psi^b (the force of Eq. (3) with
-    sum_i w_i e_i e_i = c_s^2 I)."""
+    sum_i w_i e_i e_i = c_s^2 I), plus g^{cc} c_s^2 (Psi^c)^2 / 2 for self couplings."""
     pr = 1.0 - np.exp(-np.asarray(rho_r, np.float64))
     pb = 1.0 - np.exp(-np.asarray(rho_b, np.float64))
-    return CS2 * (np.asarray(rho_r, np.float64) + rho_b) + G * CS2 * pr * pb
+    return (CS2 * (np.asarray(rho_r, np.float64) + rho_b) + G * CS2 * pr * pb
+            + 0.5 * CS2 * (G_rr * pr * pr + G_bb * pb * pb))
 
 
 def _droplet_params(n, G, tau, geometry=0, R_H=0.0, rho_H=0.03, storage="f32"):
@@ -57,6 +58,31 @@ def surface_tension(radii=(8.0, 12.0, 16.0), margin=12, steps=4000, G=3.6, tau=1
         m = n // 2
         inv_r.append(1.0 / d["radius"])
         dp.append(float(bulk_pressure(rr[m, m, m], rb[m, m, m], G) - bulk_pressure(rr[0, 0, 0], rb[0, 0, 0], G)))
+    slope, icpt = np.polyfit(inv_r, dp, 1)
+    return dict(gamma=slope / 2.0, intercept=icpt, inv_radius=inv_r, pressure_jump=dp)
+
+
+def single_component_laplace(g, rho_l, rho_g, radii=(8.0, 12.0, 16.0), margin=12, steps=3000):
+    """Laplace test of the multiphase pseudopotential model (component b absent,
+    self coupling g^{rr} = g, no cross coupling): a liquid droplet (rho_l) in its
+    vapour (rho_g) in a periodic box of edge 2 R + 2 margin settles for `steps`
+    steps; R is the radius of the volume where rho > (rho_l + rho_g) / 2. Returns
+    gamma = slope / 2 of the pressure jump against 1/R and the fit data."""
+    inv_r, dp = [], []
+    for R0 in radii:
+        n = int(2 * R0 + 2 * margin)
+        c = (n - 1) / 2.0
+        z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+        inside = (x - c) ** 2 + (y - c) ** 2 + (z - c) ** 2 < R0 * R0
+        lat = Lattice(dict(nx=n, ny=n, nz=n, G=0.0, G_rr=g, geometry=0))
+        lat.init_fields(np.where(inside, rho_l, rho_g).astype(np.float32), np.zeros((n, n, n), np.float32))
+        lat.step(steps)
+        rr, _ = lat.read_fields()
+        lat.close()
+        m = n // 2
+        vol = float(np.count_nonzero(rr > 0.5 * (rho_l + rho_g)))
+        inv_r.append(1.0 / equivalent_radius(vol))
+        dp.append(float(bulk_pressure(rr[m, m, m], 0.0, 0.0, G_rr=g) - bulk_pressure(rr[0, 0, 0], 0.0, 0.0, G_rr=g)))
     slope, icpt = np.polyfit(inv_r, dp, 1)
     return dict(gamma=slope / 2.0, intercept=icpt, inv_radius=inv_r, pressure_jump=dp)
 

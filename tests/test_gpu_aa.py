@@ -41,6 +41,10 @@ def _cases():
     p.update(nx=1, ny=3, nz=12, sink_z0=11, wall_z0=5, wall_thickness=1)
     i.update(film_z=4)
     out["thin_column_mid_wall"] = (p, i)
+    p, i = droplet(20, 5.0, 3, spherical_sink=True)
+    p.update(nx=20, ny=12, nz=16, sphere_cx=10.0, sphere_cy=6.0, sphere_cz=8.0, R_H=7.0, G_rr=-1.1, G_bb=0.5)
+    i.update(cx=10.0, cy=6.0, cz=8.0, radius=4.0)
+    out["self_couplings_sphere_sink"] = (p, i)
     return out
 
 

@@ -33,7 +33,7 @@ def _members():
     p.update(tau_r=0.9, tau_b=1.15, G=3.7)
     out.append((p, i))
     p, i = droplet(24, 6.0, 9)
-    p.update(geometry=0, nx=50, ny=17, nz=21)
+    p.update(geometry=0, nx=50, ny=17, nz=21, G_rr=-0.8, G_bb=0.4)  # with self couplings
     i.update(cx=25.0, cy=8.0, cz=10.0)
     out.append((p, i))
     p, i = droplet(33, 7.0, 13)

@@ -50,6 +50,7 @@ GEOMS = {
     "seam_sink_2layers": dict(geometry=1, sink_z0=-1, sink_layers=2, rho_H=0.02),
     "sphere_sink": dict(geometry=2, sphere_cx=10.0, sphere_cy=5.5, sphere_cz=4.0, R_H=4.5, rho_H=0.025),
     "unequal_tau": dict(tau_r=0.8, tau_b=1.3, G=2.5),
+    "self_couplings": dict(G=2.0, G_rr=-1.3, G_bb=0.6, tau_r=0.9),  # Eq. (3) summed over cbar = c too
 }
 # nx not a multiple of 4: per-thread pulls; nx a multiple of 8: staged rows (FP32 and FP16/BF16)
 SHAPES = [(37, 13, 11), (5, 3, 4), (1, 6, 9), (70, 9, 8), (33, 17, 5),
