@@ -41,6 +41,8 @@ WORKLOADS = {
     "film_4x4x128": lambda **kw: film_4x4x128(**kw),
     "droplet_128": lambda **kw: droplet(128, 24.0, 1, **kw),
     "droplet_512": lambda **kw: droplet(512, 96.0, 2, **kw),
+    # the same recipe at 1024^3 (R/N = 0.1875): in FP32 it fits one GPU only in place
+    "droplet_1024": lambda **kw: droplet(1024, 192.0, 2, **kw),
 }
 
 

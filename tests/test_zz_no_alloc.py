@@ -40,14 +40,16 @@ def _close(a, b, rel):
     return abs(a - b) <= rel * max(1.0, abs(b))
 
 
-@pytest.mark.parametrize("case", ["droplet_sphere_sink", "film_wall_sink"])
+@pytest.mark.parametrize("case", ["droplet_sphere_sink", "film_wall_sink", "droplet_sphere_sink_in_place"])
 def test_noalloc_matches_diagnostics_twice(sc, case):
     import torch
     from paper_1701_03637_gb300.workloads import droplet, film_4x4x128
-    if case == "droplet_sphere_sink":
+    if case.startswith("droplet_sphere_sink"):
         params, init = droplet(40, 9.0, 11, spherical_sink=True)
     else:
         params, init = film_4x4x128(rho_hi=0.7, rho_lo=0.04, rho_H=0.01)
+    if case.endswith("in_place"):
+        params["layout"] = "aa"  # 40 steps: even form, 65 steps: odd form
     lat = sc.Lattice(params)
     lat.init(init)
     out = torch.full((8,), float("nan"), dtype=torch.float64, device="cuda")
