@@ -212,6 +212,17 @@ def max_over_ranks(v, world, device="cpu"):
     return float(t.item())
 
 
+def sum_over_ranks(v, world, device="cpu"):
+    """The sum of every rank's value; world == 1 needs no process group."""
+    if world == 1:
+        return float(v)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def replica_value(sites_per_rank, steps, world, ms_max):
     """Whole-job MLUPS of independent replicas: every rank's site updates over
     the slowest rank's time (weak scaling)."""
@@ -400,15 +411,33 @@ def run_ensemble(args):
     import numpy as np
     import torch
 
-    import paper_1701_03637_gb300 as sc
-    from paper_1701_03637_gb300.workloads import ensemble
+    import torch.distributed as dist
 
-    if int(os.environ.get("RANK", "0")) != 0:
-        return  # independent replicas only; the ensemble line is rank 0's
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    import paper_1701_03637_gb300 as sc
+    from paper_1701_03637_gb300.workloads import ensemble, shard
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     sc.build()
-    members = ensemble(64, 3, args.storage)
-    sizes = [p["nx"] * p["ny"] * p["nz"] for p, _ in members]
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def slowest(v):
+        return max_over_ranks(v, world, "cuda")
+
+    # the 64 lattices are independent: each rank advances its share (no data exchange)
+    everything = ensemble(64, 3, args.storage)
+    all_sizes = [p["nx"] * p["ny"] * p["nz"] for p, _ in everything]
+    n_all = sum(all_sizes)
+    mine = shard(all_sizes, rank, world)
+    members = [everything[k] for k in mine]
+    sizes = [all_sizes[k] for k in mine]
     n = sum(sizes)
     arena = sum(sc.required_bytes(p) + 256 for p, _ in members) + (1 << 20)
     b = sc.Batch(arena, args.storage)
@@ -423,6 +452,8 @@ def run_ensemble(args):
     torch.cuda.synchronize()
     sampler = ClockSampler()
     time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
     t0 = time.time()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -430,11 +461,14 @@ def run_ensemble(args):
     b.step(args.steps)
     e1.record(stream)
     torch.cuda.synchronize()
+    barrier()
     t1 = time.time()
     sampler.stop()
-    ms = e0.elapsed_time(e1)
-    bad = [k for k, lat in enumerate(lats) if lat.diagnostics()["status"] != 0]
-    value = n * args.steps / (ms * 1e-3) / 1e6
+    ms = e0.elapsed_time(e1)  # this rank's launches (the roofline below is of its kernel)
+    ms_max = slowest(ms)
+    bad = [mine[k] for k, lat in enumerate(lats) if lat.diagnostics()["status"] != 0]
+    nbad = int(round(sum_over_ranks(len(bad), world, "cuda")))
+    value = n_all * args.steps / (ms_max * 1e-3) / 1e6
     peak, peak_kind = measured_peak_hbm()
     achieved = BYTES_PER_SITE[args.storage] * n / (ms * 1e-3 / args.steps) / 1e9
 
@@ -446,6 +480,7 @@ def run_ensemble(args):
         g.init(i)
         g.step(2)
         singles.append(g)
+    barrier()
     torch.cuda.synchronize()
     s0 = torch.cuda.Event(enable_timing=True)
     s1 = torch.cuda.Event(enable_timing=True)
@@ -454,8 +489,9 @@ def run_ensemble(args):
         g.step(seq_steps)
     s1.record(stream)
     torch.cuda.synchronize()
-    seq_ms = s0.elapsed_time(s1)
-    seq_value = n * seq_steps / (seq_ms * 1e-3) / 1e6
+    barrier()
+    seq_ms = slowest(s0.elapsed_time(s1))
+    seq_value = n_all * seq_steps / (seq_ms * 1e-3) / 1e6
     for g in singles:
         g.close()
 
@@ -465,6 +501,7 @@ def run_ensemble(args):
                 torch.from_numpy(np.ascontiguousarray(lat.read_fields()[1]).reshape(-1)).pin_memory()) for lat in lats]
     host_out = [(torch.empty(lat.n, dtype=torch.float32).pin_memory(),
                  torch.empty(lat.n, dtype=torch.float32).pin_memory()) for lat in lats]
+    barrier()
     torch.cuda.synchronize()
     w0 = time.perf_counter()
     for lat, (hr, hb) in zip(lats, host_in):
@@ -480,15 +517,16 @@ def run_ensemble(args):
     for lat, (hr, hb) in zip(lats, host_out):
         lat.read_fields_into(hr, hb)
     torch.cuda.synchronize()
-    wall = time.perf_counter() - w0
-    diag_bytes = ndiag * sum(lat.diag_bytes() for lat in lats)
-    e2e = {"value": n * args.steps / wall / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": 8 * n / args.steps,
-           "d2h_bytes_per_step": (8 * n + diag_bytes) / args.steps,
+    wall = slowest(time.perf_counter() - w0)
+    barrier()
+    diag_bytes = sum_over_ranks(ndiag * sum(lat.diag_bytes() for lat in lats), world, "cuda")
+    e2e = {"value": n_all * args.steps / wall / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": 8 * n_all / args.steps,
+           "d2h_bytes_per_step": (8 * n_all + diag_bytes) / args.steps,
            "includes": "init of all 64 members from pinned host densities, all steps, every member's "
                        "diagnostics every 100 steps, final densities to pinned host"}
 
     cpu = None
-    if not args.no_cpu_baseline:
+    if world == 1 and not args.no_cpu_baseline:
         cores = host_cores()
         k = int(np.argmin(np.abs(np.asarray(sizes) - np.median(sizes))))
         rate, steps = oracle_rate(members[k][0], members[k][1], 12.0, cores)
@@ -498,15 +536,23 @@ def run_ensemble(args):
     clk = sampler.summary(t0, t1)
     info = b.info()
     run_steps = 2000
-    out = {"metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": 1, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+    if rank != 0:
+        b.close()
+        dist.destroy_process_group()
+        return
+    out = {"metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+           # the 64 lattices are split over the ranks: the total work is fixed as N grows
+           "scaling": "strong" if world > 1 else "weak",
            "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
            "config": {"workload": "ensemble_64: 64 two-component D3Q19 Shan-Chen lattices, edges "
                                   "exp(U(ln 32, ln 96)) per axis, even = planar film on a wall, odd = droplet, "
                                   "g ~ U(3.2, 3.8), tau ~ U(0.8, 1.2), master seed 3",
-                      "sites": n, "lattices_per_gpu": 64, "l2": "inputs larger than L2 (no flush)",
+                      "sites": n_all, "lattices_per_gpu": len(members), "l2": "inputs larger than L2 (no flush)",
                       "tile": sc.tile_list()[tile - 1], "zchunk": zc, "items": info["items"],
-                      "parallelism": "one persistent launch per step over all members"},
+                      "parallelism": "one persistent launch per step over all members"
+                                     + (f"; members split over {world} ranks by size, no data exchange"
+                                        if world > 1 else "")},
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                         "traffic": None, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
                         "algorithmic_bytes_per_site": BYTES_PER_SITE[args.storage]},
@@ -514,12 +560,14 @@ def run_ensemble(args):
            "clocks": clk,
            "one_at_a_time": {"value": seq_value, "unit": "MLUPS", "steps": seq_steps,
                              "speedup_of_batch": value / seq_value},
-           "runs_per_hour": {"batched": 64 * 3600.0 / (ms * 1e-3 / args.steps * run_steps),
+           "runs_per_hour": {"batched": 64 * 3600.0 / (ms_max * 1e-3 / args.steps * run_steps),
                              "one_at_a_time": 64 * 3600.0 / (seq_ms * 1e-3 / seq_steps * run_steps),
                              "run": f"{run_steps} steps per lattice"},
-           "members_with_bad_status": bad}
+           "members_with_bad_status": bad, "members_with_bad_status_all_ranks": nbad}
     print(json.dumps(out))
     b.close()
+    if world > 1:
+        dist.destroy_process_group()
 
 
 def run_serve(args):

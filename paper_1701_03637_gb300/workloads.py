@@ -103,6 +103,23 @@ def ensemble(count: int = 64, seed: int = 3, storage="f32"):
     return [ensemble_member(k, rng, storage=storage) for k in range(count)]
 
 
+def shard(sizes, rank: int, world: int):
+    """Indices of the ensemble members that `rank` of `world` ranks advances: the
+    largest member first to the rank with the fewest sites so far (ties to the lower
+    rank), so every member goes to exactly one rank and the ranks' site totals differ
+    by at most the largest member. Deterministic: every rank computes the same split."""
+    if world < 1 or not 0 <= rank < world:
+        raise ValueError("rank must lie in [0, world)")
+    order = sorted(range(len(sizes)), key=lambda k: (-sizes[k], k))
+    load = [0] * world
+    owner = [0] * len(sizes)
+    for k in order:
+        r = min(range(world), key=lambda q: (load[q], q))
+        owner[k] = r
+        load[r] += sizes[k]
+    return [k for k in range(len(sizes)) if owner[k] == rank]
+
+
 def random_populations(nx, ny, nz, seed, rho=(0.6, 0.1), spread=0.3):
     """Non-equilibrium populations f[c][i][z][y][x] = rho_c * U(1-spread, 1+spread) / 19,
     float64, seeded with numpy's PCG64."""

@@ -1,7 +1,9 @@
-"""The multi-GPU form of the benchmark is independent replicas (weak scaling):
-every rank advances its own lattice, the job's time is the slowest rank's, and
-the value counts every rank's site updates. Two gloo ranks on the CPU check the
-cross-rank reduction and the whole-job value."""
+"""The multi-GPU forms of the benchmark need no data exchange: the single-lattice
+workload runs independent replicas (weak scaling: every rank advances its own
+lattice, the job's time is the slowest rank's, the value counts every rank's site
+updates), and the 64-lattice ensemble is split over the ranks by size (strong
+scaling). Two gloo ranks on the CPU check the cross-rank reductions, the whole-job
+value and the split."""
 import multiprocessing as mp
 import os
 import socket
@@ -48,3 +50,50 @@ def test_single_rank_needs_no_process_group():
     import bench
     assert bench.max_over_ranks(7.5, 1) == 7.5
     assert bench.replica_value(100, 10, 1, 1.0) == pytest.approx(1.0)
+
+
+@pytest.mark.parametrize("world", [1, 2, 3, 4, 8])
+def test_ensemble_shards_cover_every_member_once(world):
+    """The 64-lattice ensemble splits over the ranks (no data exchange between its
+    independent lattices): every member on exactly one rank, site totals within the
+    largest member of each other, the same split on every rank."""
+    from paper_1701_03637_gb300.workloads import ensemble, shard
+    sizes = [p["nx"] * p["ny"] * p["nz"] for p, _ in ensemble(64, 3)]
+    parts = [shard(sizes, r, world) for r in range(world)]
+    flat = sorted(k for part in parts for k in part)
+    assert flat == list(range(64))
+    loads = [sum(sizes[k] for k in part) for part in parts]
+    assert max(loads) - min(loads) <= max(sizes)
+    assert parts == [shard(sizes, r, world) for r in range(world)]
+    with pytest.raises(ValueError):
+        shard(sizes, world, world)
+
+
+def _ens_rank(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    from paper_1701_03637_gb300.workloads import ensemble, shard
+    sizes = [p["nx"] * p["ny"] * p["nz"] for p, _ in ensemble(64, 3)]
+    mine = shard(sizes, rank, world)
+    total = bench.sum_over_ranks(sum(sizes[k] for k in mine), world)
+    count = bench.sum_over_ranks(len(mine), world)
+    q.put((rank, total, count, sum(sizes)))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_share_the_ensemble():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_ens_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, total, count, expect in res:
+        assert total == expect and count == 64
