@@ -57,7 +57,7 @@ SHAPES = [(37, 13, 11), (5, 3, 4), (1, 6, 9), (70, 9, 8), (33, 17, 5),
           (40, 13, 11), (8, 3, 4), (4, 6, 9), (72, 9, 8), (24, 17, 5)]
 
 
-# step kernel tiles: 0 = automatic choice, k > 0 = entry k - 1 of the tile list (32x8, 32x4, 16x8, 8x4)
+# step kernel tiles: 0 = automatic choice, k > 0 = entry k - 1 of the tile list (32x8, 32x4, 16x8, 8x4, 64x4)
 KERNELS = [0, 1, 2, 4]
 
 
