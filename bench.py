@@ -212,6 +212,17 @@ def max_over_ranks(v, world, device="cpu"):
     return float(t.item())
 
 
+def gather_results(res, world):
+    """Every rank's served results, merged in request order (rank 0 reports them);
+    world == 1 needs no process group."""
+    if world == 1:
+        return sorted(res, key=lambda r: r.rid)
+    import torch.distributed as dist
+    parts = [None] * world
+    dist.all_gather_object(parts, list(res))
+    return sorted((r for part in parts for r in part), key=lambda r: r.rid)
+
+
 def sum_over_ranks(v, world, device="cpu"):
     """The sum of every rank's value; world == 1 needs no process group."""
     if world == 1:
@@ -577,15 +588,36 @@ def run_serve(args):
     import numpy as np
     import torch
 
+    import torch.distributed as dist
+
     import paper_1701_03637_gb300 as sc
-    from paper_1701_03637_gb300.serve import Request, Server, percentile, serve_one_at_a_time
+    from paper_1701_03637_gb300.serve import Request, Server, dispatch, percentile, serve_one_at_a_time
     from paper_1701_03637_gb300.workloads import request_stream
 
-    if int(os.environ.get("RANK", "0")) != 0:
-        return
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     sc.build()
     storage = args.storage if args.storage != "f32" else "f16"
+
+    def served(reqs, run):
+        """Every rank serves its round-robin share of the stream, starting together;
+        the results of all ranks, in request order."""
+        mine = dispatch(reqs, rank, world)
+        if world > 1:
+            dist.barrier()
+        return gather_results(run(mine), world)
+
+    def batched_server(cap=0):
+        def run(mine):
+            srv = Server(arena, storage, max_active_sites=cap)
+            out = srv.run(mine)
+            srv.close()
+            return out
+        return run
 
     def stream(count, rate, seed):
         return [Request(k, t, p, i, n) for k, (t, p, i, n) in
@@ -605,28 +637,20 @@ def run_serve(args):
 
     over = stream(args.requests, args.rate, 4)
     cap = 6 * 2 ** 20  # resident sites: about three 128^3 lattices, enough to fill the GPU
-    srv = Server(arena, storage, max_active_sites=cap)
     sampler = ClockSampler()
     t0 = time.time()
-    w0 = time.perf_counter()
-    res = srv.run(over)
-    wall = time.perf_counter() - w0
+    res = served(over, batched_server(cap))
     t1 = time.time()
     sampler.stop()
-    srv.close()
     batched = summary(res, max(r.finished for r in res))
-    srv = Server(arena, storage)
-    res_all = srv.run(over)
-    srv.close()
+    res_all = served(over, batched_server())
     uncapped = summary(res_all, max(r.finished for r in res_all))
 
     light = stream(max(4, args.requests // 4), args.rate / 20.0, 5)
-    srv = Server(arena, storage, max_active_sites=cap)
-    res_light = srv.run(light)
-    srv.close()
+    res_light = served(light, batched_server(cap))
     light_s = summary(res_light, max(r.finished for r in res_light))
 
-    seq = serve_one_at_a_time(over, "f32")
+    seq = served(over, lambda mine: serve_one_at_a_time(mine, "f32"))
     seq_s = summary(seq, max(r.finished for r in seq))
     # error of the served FP16 runs against the same runs in FP32 (FP32 matches the
     # FP64 oracle to 1e-4 in density after 1000 steps): the observable of each
@@ -637,14 +661,21 @@ def run_serve(args):
         errs.append(abs(a.series[-1][k] - b.series[-1][k]))
     clk = sampler.summary(t0, t1)
     work = sum(r.sites * r.steps for r in res)
-    out = {"metric": "MLUPS", "value": uncapped["mlups"], "unit": "MLUPS", "n_gpus": 1, "steps": None,
-           "warmup": 2, "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+    if rank != 0:
+        dist.destroy_process_group()
+        return
+    out = {"metric": "MLUPS", "value": uncapped["mlups"], "unit": "MLUPS", "n_gpus": world, "steps": None,
+           "warmup": 2, "ms_per_step": None, "higher_is_better": True,
+           # one stream dispatched over the ranks: the total work is fixed as N grows
+           "scaling": "strong" if world > 1 else "weak", "vs_baseline": None,
            "dtype": storage, "data": "synthetic",
            "config": {"workload": f"serve: {args.requests} requests, Poisson {args.rate}/s, cubic lattices edge "
                                   f"exp(U(ln 32, ln 160)), 2000-20000 steps, films and droplets, g ~ U(3.2, 3.8), "
                                   f"tau ~ U(0.8, 1.2), {storage} offsets, master seed 4",
                       "site_updates": work, "arena_bytes": arena, "diag_every": 100,
-                      "l2": "inputs larger than L2 (no flush)"},
+                      "l2": "inputs larger than L2 (no flush)",
+                      "parallelism": f"requests dispatched round-robin over {world} ranks, no data exchange"
+                                     if world > 1 else "one GPU"},
            "serving": {"batched": uncapped,
                        "batched_site_cap": dict(batched, max_active_sites=cap),
                        "sub_capacity": dict(light_s, rate_per_s=args.rate / 20.0),
@@ -654,6 +685,8 @@ def run_serve(args):
                                                                 "(droplets), lattice units"}},
            "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": clk}
     print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
 
 
 def main():

@@ -150,6 +150,17 @@ def serve_one_at_a_time(requests, storage="f32", diag_every: int = 100, clock=ti
     return sorted(out, key=lambda x: x.rid)
 
 
+def dispatch(requests, rank: int, world: int):
+    """Round-robin dispatch of a request stream over `world` GPUs in arrival order:
+    rank r serves requests r, r + world, r + 2 world, ... of the stream (each request
+    on exactly one rank, no data exchanged between ranks). Arrival times are kept,
+    so every rank sees its share of the stream in real time."""
+    if world < 1 or not 0 <= rank < world:
+        raise ValueError("rank must lie in [0, world)")
+    order = sorted(requests, key=lambda q: (q.arrival, q.rid))
+    return [q for k, q in enumerate(order) if k % world == rank]
+
+
 def percentile(values, q):
     v = sorted(values)
     if not v:

@@ -97,3 +97,37 @@ def test_two_gloo_ranks_share_the_ensemble():
         assert p.exitcode == 0
     for rank, total, count, expect in res:
         assert total == expect and count == 64
+
+
+def _serve_rank(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    from paper_1701_03637_gb300.serve import Request, Result, dispatch
+    reqs = [Request(k, 0.1 * k, {}, {}, 100) for k in range(7)]
+    mine = dispatch(reqs, rank, world)
+    res = [Result(r.rid, r.arrival, r.arrival, r.arrival + 1.0 + rank, r.steps, 10) for r in mine]
+    merged = bench.gather_results(res, world)
+    q.put((rank, [(r.rid, r.finished) for r in merged]))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_serve_one_stream():
+    """A served stream dispatched round-robin over two ranks: every rank's results
+    come back to every rank, merged in request order."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_serve_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    expect = [(k, 0.1 * k + 1.0 + (k % 2)) for k in range(7)]
+    for rank, merged in res:
+        assert [r for r, _ in merged] == list(range(7))
+        assert [f for _, f in merged] == pytest.approx([f for _, f in expect])

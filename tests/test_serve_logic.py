@@ -124,3 +124,16 @@ def test_site_cap_limits_the_active_set_but_always_admits_one():
     res = srv.run(reqs, clock=clock, sleep=clock.sleep)
     assert all(len(m) == 1 for _, m in fb.log)  # 1000 + 1000 > 1500; 8000 alone is admitted
     assert res[1].admitted >= res[0].finished and res[2].admitted >= res[1].finished
+
+
+@pytest.mark.parametrize("world", [1, 2, 3, 8])
+def test_dispatch_serves_every_request_once_in_arrival_order(world):
+    from paper_1701_03637_gb300.serve import Request, dispatch
+    reqs = [Request(k, t, {}, {}, 100) for k, t in enumerate([0.5, 0.1, 0.3, 0.3, 0.9, 0.2, 0.7])]
+    parts = [dispatch(reqs, r, world) for r in range(world)]
+    assert sorted(q.rid for part in parts for q in part) == list(range(len(reqs)))
+    order = sorted(reqs, key=lambda q: (q.arrival, q.rid))
+    for r, part in enumerate(parts):
+        assert [q.rid for q in part] == [q.rid for q in order[r::world]]
+    with pytest.raises(ValueError):
+        dispatch(reqs, world, world)
