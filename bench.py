@@ -657,8 +657,11 @@ def run_serve(args):
     # run's last record (interface position for films, radius for droplets)
     errs = []
     for a, b in zip(res, seq):
+        if a.status or b.status:
+            continue  # an evicted run has no final observable (counted in failed_runs)
         k = 1 if over[a.rid].init["shape"] == 0 else 2
         errs.append(abs(a.series[-1][k] - b.series[-1][k]))
+    failed = {"batched": sum(1 for r in res if r.status), "one_at_a_time_fp32": sum(1 for r in seq if r.status)}
     clk = sampler.summary(t0, t1)
     work = sum(r.sites * r.steps for r in res)
     if rank != 0:
@@ -680,7 +683,9 @@ def run_serve(args):
                        "batched_site_cap": dict(batched, max_active_sites=cap),
                        "sub_capacity": dict(light_s, rate_per_s=args.rate / 20.0),
                        "one_at_a_time_fp32": seq_s,
-                       "observable_abs_error_vs_fp32": {"max": max(errs), "median": percentile(errs, 50),
+                       "failed_runs": failed,
+                       "observable_abs_error_vs_fp32": {"max": max(errs, default=float("nan")),
+                                                        "median": percentile(errs, 50),
                                                         "what": "final interface position (films) or radius "
                                                                 "(droplets), lattice units"}},
            "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": clk}

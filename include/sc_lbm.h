@@ -91,7 +91,7 @@ extern "C" {
 typedef struct sc_params {
   int32_t nx, ny, nz;             /* lattice extent, each >= 1 */
   double tau_r, tau_b;            /* BGK relaxation times (> 0.5); the paper uses 1 */
-  double G;                       /* g^{c cbar} of Eq. (3) */
+  double G;                       /* cross coupling g^{rb} = g^{br} of Eq. (3) */
   double rho_H;                   /* imposed density of component r at sink sites */
   int32_t geometry;               /* SC_GEOM_* */
   int32_t sink_z0, sink_layers;   /* planar sink: first plane and number of planes (1 or 2) */

@@ -11,7 +11,9 @@ steps: interface position (film) or droplet radius, the last step's evaporated
 mass (the flux through the sink) and the cumulative evaporated mass
 (arXiv:1701.03637 Sec. III). A finished run leaves the batch at once, freeing
 its range for the next request. Every member computes exactly what a lone run
-computes, so a result does not depend on the mix it was served in.
+computes, so a result does not depend on the mix it was served in. A run whose
+diagnostics report a non-finite density or a negative sink complement is
+evicted at that record and reported with the status; the others carry on.
 """
 from __future__ import annotations
 
@@ -39,17 +41,23 @@ class Result:
     steps: int
     sites: int
     series: list = field(default_factory=list)  # (step, interface_z, radius, flux_last, evaporated_mass, mass_r)
+    status: int = 0  # diagnostics status that ended the run early (SC_ENONFINITE, SC_ESINKNEG); 0 = completed
 
     @property
     def latency(self) -> float:
         return self.finished - self.arrival
 
 
-def _record(lat, series):
+def _record(lat, res):
+    """Append the run's diagnostics to its series; a non-zero status (a non-finite
+    density or a negative sink complement) ends the run: it is stored in the result
+    and returned, and the caller evicts the run."""
     d = lat.diagnostics()
     if d["status"] != 0:
-        raise RuntimeError(f"run diverged: diagnostics status {d['status']} at step {d['step']}")
-    series.append((d["step"], d["interface_z"], d["radius"], d["flux_last"], d["evaporated_mass"], d["mass_r"]))
+        res.status = int(d["status"])
+        return res.status
+    res.series.append((d["step"], d["interface_z"], d["radius"], d["flux_last"], d["evaporated_mass"], d["mass_r"]))
+    return 0
 
 
 class Server:
@@ -74,7 +82,8 @@ class Server:
         self.batch.close()
 
     def run(self, requests, clock=time.perf_counter, sleep=time.sleep):
-        """Serve `requests` (sorted by arrival); returns the Results in request order."""
+        """Serve `requests` (sorted by arrival); returns the Results in request order
+        (a run evicted for a bad diagnostics status has Result.status != 0)."""
         pending = sorted(requests, key=lambda r: r.arrival)
         active = {}   # slot -> (request, lattice, result, steps done)
         done = {}
@@ -100,7 +109,11 @@ class Server:
                 lat.init(r.init)
                 self.batch.set_steps(slot, r.steps)
                 res = Result(r.rid, r.arrival, clock() - t0, 0.0, r.steps, lat.n)
-                _record(lat, res.series)
+                if _record(lat, res):  # a state that is already bad: reported, never stepped
+                    res.finished = clock() - t0
+                    done[r.rid] = res
+                    self.batch.remove(slot)
+                    continue
                 active[slot] = (r, lat, res, 0)
             if not active:
                 if pending:
@@ -112,9 +125,8 @@ class Server:
             for slot in list(active):
                 r, lat, res, d = active[slot]
                 d += k
-                if d % self.diag_every == 0 or d == r.steps:
-                    _record(lat, res.series)
-                if d == r.steps:
+                failed = (d % self.diag_every == 0 or d == r.steps) and _record(lat, res) != 0
+                if d == r.steps or failed:  # finished, or evicted with its status
                     res.finished = clock() - t0
                     done[r.rid] = res
                     self.batch.remove(slot)
@@ -137,13 +149,13 @@ def serve_one_at_a_time(requests, storage="f32", diag_every: int = 100, clock=ti
         lat = Lattice(dict(r.params, storage=storage))
         lat.init(r.init)
         res = Result(r.rid, r.arrival, clock() - t0, 0.0, r.steps, lat.n)
-        _record(lat, res.series)
-        done = 0
+        done = r.steps if _record(lat, res) else 0
         while done < r.steps:
             k = min(diag_every - done % diag_every, r.steps - done)
             lat.step(k)
             done += k
-            _record(lat, res.series)
+            if _record(lat, res):
+                break
         res.finished = clock() - t0
         lat.close()
         out.append(res)

@@ -21,13 +21,13 @@ def _alone(sc, req, storage, diag_every):
     lat = sc.Lattice(dict(req.params, storage=storage))
     lat.init(req.init)
     res = Result(req.rid, 0.0, 0.0, 0.0, req.steps, lat.n)
-    _record(lat, res.series)
+    assert _record(lat, res) == 0
     done = 0
     while done < req.steps:
         k = min(diag_every - done % diag_every, req.steps - done)
         lat.step(k)
         done += k
-        _record(lat, res.series)
+        assert _record(lat, res) == 0
     lat.close()
     return res
 
@@ -46,7 +46,7 @@ def test_results_are_the_same_alone_and_in_the_mix(sc, storage):
     assert waited, "the arena should have made some request wait"
     for r, q in zip(res, reqs):
         ref = _alone(sc, q, storage, 50)
-        assert len(r.series) == len(ref.series)
+        assert r.status == 0 and len(r.series) == len(ref.series)
         for a, b in zip(r.series, ref.series):
             step, iz, rad, flux, evap, mr = a
             assert (step, iz, rad, mr) == (b[0], b[1], b[2], b[5]), (q.rid, a, b)

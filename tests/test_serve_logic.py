@@ -9,28 +9,31 @@ from paper_1701_03637_gb300.serve import Request, Server, percentile
 
 
 class FakeLattice:
-    def __init__(self, n):
+    def __init__(self, n, fail=None):
         self.n = n
         self.step_count = 0
+        self.fail = fail or {}  # seed -> first step whose diagnostics report SC_ENONFINITE
 
     def init(self, init):
         self.seed = init["seed"]
 
     def diagnostics(self):
+        bad = self.seed in self.fail and self.step_count >= self.fail[self.seed]
         return dict(step=self.step_count, interface_z=float(self.seed), radius=0.0, flux_last=0.0,
-                    evaporated_mass=0.0, mass_r=1.0, status=0)
+                    evaporated_mass=0.0, mass_r=1.0, status=-4 if bad else 0)
 
 
 class FakeBatch:
     """Arena of `capacity` units (a lattice of n sites takes n units); each step
     costs 1 ms on the fake clock per member."""
 
-    def __init__(self, capacity, clock):
+    def __init__(self, capacity, clock, fail=None):
         self.capacity = capacity
         self.clock = clock
         self.members = {}
         self.limits = {}
         self.log = []
+        self.fail = fail
 
     def used(self):
         return sum(l.n for l in self.members.values())
@@ -42,7 +45,7 @@ class FakeBatch:
         slot = 0
         while slot in self.members:
             slot += 1
-        self.members[slot] = FakeLattice(n)
+        self.members[slot] = FakeLattice(n, self.fail)
         self.limits[slot] = None
         return slot, self.members[slot]
 
@@ -137,3 +140,22 @@ def test_dispatch_serves_every_request_once_in_arrival_order(world):
         assert [q.rid for q in part] == [q.rid for q in order[r::world]]
     with pytest.raises(ValueError):
         dispatch(reqs, world, world)
+
+
+def test_a_failing_run_is_evicted_and_reported_while_the_others_finish():
+    """Failure detection on the host: a run whose diagnostics report a non-finite
+    density (status -4, injected by the fake lattice at step 200) leaves the batch at
+    that record with its status; it is never stepped again and the others complete."""
+    clock = Clock()
+    batch = FakeBatch(10 ** 6, clock, fail={1: 200, 3: 0})
+    srv = Server(0, batch=batch, diag_every=100)
+    reqs = [_req(0, 0.0, 10, 500), _req(1, 0.0, 10, 500), _req(2, 0.0, 10, 300), _req(3, 0.0, 10, 400)]
+    res = srv.run(reqs, clock=clock, sleep=clock.sleep)
+    by = {r.rid: r for r in res}
+    assert [r.rid for r in res] == [0, 1, 2, 3]
+    assert by[1].status == -4 and [s[0] for s in by[1].series] == [0, 100]
+    assert by[3].status == -4 and by[3].series == []  # bad from the start: reported, never stepped
+    for rid, steps in ((0, 500), (2, 300)):
+        assert by[rid].status == 0 and by[rid].series[-1][0] == steps
+    assert not batch.members
+    assert by[1].finished < by[0].finished
