@@ -500,6 +500,7 @@ int sc_batch_configure(sc_batch* b, int32_t tile, int32_t zchunk) {
 }
 
 int sc_batch_step(sc_batch* b, int64_t nsteps) {
+  Range range("sc_batch_step");
   if (!b) return fail(SC_EINVAL, "NULL batch");
   if (nsteps < 0) return fail(SC_EINVAL, "nsteps must be >= 0");
   if (b->tile < 0) { b->tile = batch_default_tile(b); b->dirty = true; }
@@ -524,6 +525,7 @@ int sc_batch_step(sc_batch* b, int64_t nsteps) {
 }
 
 int sc_batch_tune(sc_batch* b, int32_t trials, int32_t* tile, int32_t* zchunk) {
+  Range range("sc_batch_tune");
   if (!b) return fail(SC_EINVAL, "NULL batch");
   if (trials < 1) trials = 3;
   trials = std::min(trials, kBatchGraphLen);

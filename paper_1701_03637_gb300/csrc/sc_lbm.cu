@@ -13,6 +13,8 @@
 #include <type_traits>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "sc_kernels.cuh"
 #include "sc_lbm.h"
 
@@ -42,6 +44,15 @@ constexpr int kTileX[kNumTiles] = {32, 32, 16, 8, 64};
 constexpr int kTileY[kNumTiles] = {8, 4, 8, 4, 4};
 
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+// NVTX range over a host call of the C ABI, for Nsight timelines (a no-op when no
+// tool is attached).
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
 long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
 int wrap_host(int v, int n) { return ((v % n) + n) % n; }
 
@@ -976,6 +987,7 @@ int sc_lbm_sync(sc_lbm* h) {
 }
 
 int sc_lbm_init(sc_lbm* h, const sc_init* in) {
+  Range range("sc_lbm_init");
   if (!h || !in) return fail(SC_EINVAL, "NULL argument");
   if (in->shape < 0 || in->shape > 1) return fail(SC_EINVAL, "unknown shape %d", in->shape);
   if (!std::isfinite(in->rho_hi) || !std::isfinite(in->rho_lo) || !std::isfinite(in->noise_amp))
@@ -990,6 +1002,7 @@ int sc_lbm_init(sc_lbm* h, const sc_init* in) {
 }
 
 int sc_lbm_init_fields(sc_lbm* h, const float* rr, const float* rb) {
+  Range range("sc_lbm_init_fields");
   if (!h || !rr || !rb) return fail(SC_EINVAL, "NULL argument");
   const long long n = h->lay.nsites;
   float* st = h->stage();
@@ -1034,6 +1047,7 @@ static int ensure_graph(sc_lbm* h) {
 static void batch_touch(sc_batch* b);  // the member's buffer parity changed outside the batch
 
 int sc_lbm_step(sc_lbm* h, int64_t nsteps) {
+  Range range("sc_lbm_step");
   if (!h) return fail(SC_EINVAL, "NULL handle");
   if (nsteps < 0) return fail(SC_EINVAL, "nsteps must be >= 0");
   if (h->owner && nsteps > 0) batch_touch(h->owner);
@@ -1067,6 +1081,7 @@ int sc_lbm_read_fields_device(sc_lbm* h, float* rr, float* rb) {
 }
 
 int sc_lbm_read_fields(sc_lbm* h, float* rr, float* rb) {
+  Range range("sc_lbm_read_fields");
   if (!h || !rr || !rb) return fail(SC_EINVAL, "NULL argument");
   int rc = canonical(h, 0, h->lay.nsites, h->stage(), h->lay.stage_n, nullptr, 0);
   if (rc) return rc;
@@ -1078,6 +1093,7 @@ int sc_lbm_read_fields(sc_lbm* h, float* rr, float* rb) {
 }
 
 int sc_lbm_read_populations(sc_lbm* h, double* f) {
+  Range range("sc_lbm_read_populations");
   if (!h || !f) return fail(SC_EINVAL, "NULL argument");
   const long long n = h->lay.nsites, slab = slab_sites(h);
   std::vector<float> tmp;
@@ -1095,6 +1111,7 @@ int sc_lbm_read_populations(sc_lbm* h, double* f) {
 }
 
 int sc_lbm_write_populations(sc_lbm* h, const double* f) {
+  Range range("sc_lbm_write_populations");
   if (!h || !f) return fail(SC_EINVAL, "NULL argument");
   const long long n = h->lay.nsites, slab = slab_sites(h);
   std::vector<float> tmp;
@@ -1152,6 +1169,7 @@ int sc_lbm_profile(sc_lbm* h, double* phi) {
 }
 
 int sc_lbm_diagnostics(sc_lbm* h, sc_diag* d) {
+  Range range("sc_lbm_diagnostics");
   if (!h || !d) return fail(SC_EINVAL, "NULL argument");
   int rc = run_diag(h);
   if (rc) return rc;
@@ -1196,6 +1214,7 @@ int sc_lbm_diagnostics(sc_lbm* h, sc_diag* d) {
 }
 
 int sc_lbm_diagnostics_noalloc(sc_lbm* h, double* out_dev) {
+  Range range("sc_lbm_diagnostics_noalloc");
   if (!h || !out_dev) return fail(SC_EINVAL, "NULL argument");
   const long long need = (long long)h->p.nz * h->lay.diag_nsplit * kDiagFields;
   if (need > kNoAllocScratch)
@@ -1228,6 +1247,7 @@ int sc_lbm_launch_info(sc_lbm* h, int32_t* tx, int32_t* ty, int32_t* zchunk, int
 }
 
 int sc_lbm_tune(sc_lbm* h, int32_t trials, int32_t* tile, int32_t* zchunk) {
+  Range range("sc_lbm_tune");
   if (!h) return fail(SC_EINVAL, "NULL handle");
   if (h->lay.aa) {  // one configuration, and no spare buffer for trial launches
     if (tile) *tile = 0;
