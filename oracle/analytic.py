@@ -1,7 +1,7 @@
 """Analytic laws of arXiv:1701.03637 Sec. III, written out in numpy.
 
 TEST INFRASTRUCTURE ONLY (part of the oracle): the tests use these closed forms
-and ODE solutions to judge the simulated physics.
+and ODE solutions to check the simulated physics.
 
 Readings where the printed formulas are garbled (each also listed in the design
 notes):

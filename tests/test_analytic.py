@@ -15,7 +15,8 @@ def test_diffusion_coefficient_limits():
     # D^c = D^{cc} - D^{c cbar} (Sec. III A, grad rho^cbar = -grad rho^c)
     dcc, dccb = A.diffusion_matrix(0.036, 0.704, 3.6)
     assert abs((dcc - dccb) - A.diffusion_coefficient(0.036, 0.704, 3.6)) < 1e-15
-    # the survey's value at the film's printed equilibrium densities
+    # an independent evaluation of the Sec. III A formula at the film's printed
+    # equilibrium densities (0.036, 0.704)
     assert abs(A.diffusion_coefficient(0.036, 0.704, 3.6) - 0.11824) < 1e-5
 
 

@@ -15,9 +15,10 @@ import os
 import numpy as np
 import pytest
 
+from tests.results import save
+
 pytestmark = pytest.mark.gpu
 
-OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "..", "gpurun_out")
 
 
 @pytest.fixture(scope="module")
@@ -47,12 +48,7 @@ def test_droplet_radius_follows_the_laplace_corrected_law(sc):
     law0 = _law_dR(A, R_t0, t1 - t0, R0, 0.0, run)  # without the Laplace correction
     rec = dict(gamma=gamma, laplace=lap, R0=R0, R_t0=R_t0, dR_sim=sim, dR_law=law, dR_law_no_laplace=law0,
                t=t.tolist(), R=R.tolist(), rho_ma0=run["rho_ma0"], rho_mi0=run["rho_mi0"], rho_b_out=run["rho_b_out"])
-    try:
-        os.makedirs(OUT, exist_ok=True)
-        with open(os.path.join(OUT, "droplet_law_96.json"), "w") as fh:
-            json.dump(rec, fh, indent=1)
-    except OSError:
-        pass
+    save("droplet_law_96.json", rec)
     print(json.dumps({k: v for k, v in rec.items() if k not in ("t", "R", "laplace")}))
     assert sim < 0
     assert abs(sim - law) < 0.10 * abs(law), (sim, law, law0)

@@ -17,11 +17,12 @@ import os
 import numpy as np
 import pytest
 
+from tests.results import save
+
 pytestmark = [pytest.mark.gpu,
               pytest.mark.skipif(os.environ.get("SC_PAPER_SCALE") != "1",
                                  reason="paper-scale run (about ten GPU minutes): set SC_PAPER_SCALE=1")]
 
-OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "..", "gpurun_out")
 STEPS = 250000
 WINDOW = (50000.0, 250000.0)
 
@@ -62,12 +63,7 @@ def test_paper_scale_droplet_follows_the_law(sc, gamma, rho_H):
                dR_law_no_laplace=law0, rho_ma0=run["rho_ma0"], rho_mi0=run["rho_mi0"],
                rho_b_out=run["rho_b_out"], R_H=run["R_H"], t=t.tolist(), R=R.tolist(),
                evaporated_mass=run["evaporated_mass"].tolist())
-    try:
-        os.makedirs(OUT, exist_ok=True)
-        with open(os.path.join(OUT, f"droplet_law_256_{rho_H}.json"), "w") as fh:
-            json.dump(rec, fh, indent=1)
-    except OSError:
-        pass
+    save(f"droplet_law_256_{rho_H}.json", rec)
     print(json.dumps({k: v for k, v in rec.items() if k not in ("t", "R", "evaporated_mass")}))
     assert sim < 0
     assert abs(sim - law) < 0.10 * abs(law), (sim, law, law0)

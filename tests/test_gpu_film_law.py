@@ -15,9 +15,10 @@ import os
 import numpy as np
 import pytest
 
+from tests.results import save
+
 pytestmark = pytest.mark.gpu
 
-OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "..", "gpurun_out")
 
 
 @pytest.fixture(scope="module")
@@ -46,12 +47,7 @@ def test_film_interface_follows_the_evaporation_law(sc, rho_H, steps):
     sim = float(x[-1]) - x0
     rec = dict(rho_H=rho_H, D=D, x0=x0, T=T, dx_sim=sim, dx_law=law, dx_printed=printed, rho_ma=run["rho_ma"],
                rho_mi=run["rho_mi"], rho_b_vap=run["rho_b_vap"], t=t.tolist(), x_I=x.tolist())
-    try:
-        os.makedirs(OUT, exist_ok=True)
-        with open(os.path.join(OUT, f"film_law_{rho_H}.json"), "w") as fh:
-            json.dump(rec, fh, indent=1)
-    except OSError:
-        pass
+    save(f"film_law_{rho_H}.json", rec)
     print(json.dumps({k: v for k, v in rec.items() if k not in ("t", "x_I")}))
     assert sim < 0
     # measured: 3.5% (rho_H = 0.02), 6.7% (0.01; the vapour D^c rises towards the sink)

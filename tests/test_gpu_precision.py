@@ -12,15 +12,15 @@ density effect after n steps is of order 2^-12 sqrt(n) ~ 8e-3 at n = 1000 and
 is damped where the dynamics is diffusive; BF16 has 8 significant bits (8x
 FP16). The tests assert those orders and record the measured values.
 """
-import json
 import os
 
 import numpy as np
 import pytest
 
+from tests.results import save
+
 pytestmark = pytest.mark.gpu
 
-RESULTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "..", "gpurun_out")
 
 
 @pytest.fixture(scope="module")
@@ -58,12 +58,7 @@ def _study(sc, oracle_mod, n, steps):
 
 
 def _record(name, out):
-    try:
-        os.makedirs(RESULTS, exist_ok=True)
-        with open(os.path.join(RESULTS, f"precision_{name}.json"), "w") as fh:
-            json.dump(out, fh, indent=1)
-    except OSError:
-        pass
+    save(f"precision_{name}.json", out)
 
 
 def test_precision_vs_oracle_64(sc, oracle_mod):
