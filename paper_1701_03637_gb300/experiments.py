@@ -186,8 +186,10 @@ def paper_flux_z(f, c, w, G):
     the velocities of Eq. (velw) at tau = 1: U = (m^r + m^b + (F^r + F^b) / 2) /
     (rho^r + rho^b) and U^r = (m^r + F^r + rho^r u') / (2 rho^r), u' the common
     velocity and F^c = -g Psi^c(x) sum_i w_i Psi^cbar(x + e_i) e_i (Eq. (3),
-    periodic neighbours; solid sites have rho = Psi = 0). f: canonical populations
-    [2][19][z][y][x] (FP64); c, w: the library's direction table."""
+    periodic neighbours; solid sites have rho = Psi = 0; the paper's cross coupling
+    only). f: canonical populations [2][19][z][y][x] (FP64); c, w: the library's
+    direction table. Equal to the oracle's evaluation to 1e-14
+    (tests/test_flux_definition.py)."""
     rho = f.sum(axis=1)
     m = np.tensordot(c.astype(np.float64).T, f, axes=([1], [1]))  # [3][2][z][y][x]
     psi = -np.expm1(-rho)
