@@ -71,10 +71,21 @@ def describe(name, params, storage):
     n = params["nx"]
     geom = {0: "periodic", 1: f"planar sink z={params.get('sink_z0')} x{params.get('sink_layers')} layers",
             2: f"spherical sink R_H={params.get('R_H')}"}[params.get("geometry", 0)]
-    return (f"{name}: {params['nx']}x{params['ny']}x{params['nz']} two-component D3Q19 Shan-Chen droplet, "
+    shape = "film on a wall" if params.get("wall_thickness", 0) else "droplet"
+    return (f"{name}: {params['nx']}x{params['ny']}x{params['nz']} two-component D3Q19 Shan-Chen {shape}, "
             f"{geom}, tau=1, G=3.6, rho_H={params['rho_H']}, {storage} populations, "
             + ("one lattice in place (AA: Psi pass + collision)" if params.get("layout") == "aa"
                else "two-lattice pull"))
+
+
+ENSEMBLE_DESC = ("ensemble_64: 64 two-component D3Q19 Shan-Chen lattices, edges exp(U(ln 32, ln 96)) per axis, "
+                 "even = planar film on a wall, odd = droplet, g ~ U(3.2, 3.8), tau ~ U(0.8, 1.2), master seed 3")
+
+
+def serve_desc(args, storage):
+    return (f"serve: {args.requests} requests, Poisson {args.rate}/s, cubic lattices edge exp(U(ln 32, ln 160)), "
+            f"2000-20000 steps, films and droplets, g ~ U(3.2, 3.8), tau ~ U(0.8, 1.2), {storage} offsets, "
+            f"master seed 4")
 
 
 def source_digest():
@@ -240,39 +251,78 @@ def replica_value(sites_per_rank, steps, world, ms_max):
     return sites_per_rank * steps * world / (ms_max * 1e-3) / 1e6
 
 
+def reference_lattices(args):
+    """The lattices the oracle arm steps, each once per benchmark step: the workload's
+    own lattice when it is small (the 4x4x128 film), a centred crop of a droplet
+    workload sized to the time budget (same geometry and parameters, radius scaled),
+    or, for the ensemble and the served stream, the workload's own lattices smallest
+    first up to that size. Returns (lattices, sample description, workload label)."""
+    from paper_1701_03637_gb300.workloads import WORKLOADS, droplet, ensemble, request_stream
+    cores = host_cores()
+    # calibrate on a 24^3 droplet, then size the sample so W + K steps take about 90 s
+    p_probe, i_probe = droplet(24, 4.5, 1)
+    rate, _ = oracle_rate(p_probe, i_probe, 0.5, cores)
+    budget = max(512.0, rate * 1e6 * 90.0 / max(1, args.steps + args.warmup))
+    name = args.workload
+    if name in ("ensemble_64", "serve"):
+        if name == "ensemble_64":
+            pool = ensemble(64, 3, "f32")
+        else:
+            pool = [(p, i) for _, p, i, _ in request_stream(args.requests, args.rate, 4, storage="f32")]
+        pool = sorted(pool, key=lambda m: m[0]["nx"] * m[0]["ny"] * m[0]["nz"])
+        chosen, total = [], 0
+        for p, i in pool:
+            n = p["nx"] * p["ny"] * p["nz"]
+            if chosen and total + n > budget:
+                break
+            chosen.append((p, i))
+            total += n
+        label = ENSEMBLE_DESC if name == "ensemble_64" else serve_desc(args, args.storage if args.storage != "f32"
+                                                                        else "f16")
+        return chosen, (f"FP64 oracle (plain C, OpenMP) on the {len(chosen)} smallest lattices of the {name} "
+                        f"workload ({total} sites), one oracle step of each per benchmark step"), label
+    params, init = WORKLOADS[name](storage="f32")
+    n_full = params["nx"] * params["ny"] * params["nz"]
+    if n_full <= budget or init["shape"] == 0:
+        return [(params, init)], (f"FP64 oracle (plain C, OpenMP) on the full {params['nx']}x{params['ny']}x"
+                                  f"{params['nz']} lattice of {name}, one oracle step per benchmark step"), \
+            describe(name, params, args.storage)
+    edge = int(max(8, min(params["nx"], round(budget ** (1.0 / 3.0)))))
+    scale = edge / params["nx"]
+    p, i = droplet(edge, init["radius"] * scale, 1, rho_H=params["rho_H"])
+    return [(p, i)], (f"FP64 oracle (plain C, OpenMP) on a {edge}^3 crop of the {name} workload (same geometry "
+                      f"and parameters, radius scaled), one oracle step per benchmark step"), \
+        describe(name, params, args.storage)
+
+
 def run_reference(args):
-    """The oracle arm: FP64 plain-C oracle on the host cores, one oracle time step of a
-    bounded crop of the workload per benchmark step."""
+    """The oracle arm: the FP64 plain-C oracle on the host cores, one oracle time step
+    of a bounded sample of the workload per benchmark step (reference_lattices)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    from paper_1701_03637_gb300.workloads import droplet
-    params, init = workload(args.workload, args.storage)
-    n_full = params["nx"]
-    cores = host_cores()
-    # calibrate on a small crop, then size the crop so W + K steps take about 90 s
-    probe_edge = 24
-    p_probe, i_probe = droplet(probe_edge, 24.0 * probe_edge / n_full, 1)
-    rate, _ = oracle_rate(p_probe, i_probe, 0.5, cores)
-    sites = rate * 1e6 * 90.0 / max(1, args.steps + args.warmup)
-    edge = int(max(8, min(n_full, round(sites ** (1.0 / 3.0)))))
-    p, i = droplet(edge, 24.0 * edge / n_full, 1)
     import oracle
+    lattices, sample, label = reference_lattices(args)
+    cores = host_cores()
     oracle.set_threads(cores)
-    o = oracle.Lattice(p)
-    o.init_shape(i)
-    o.step(args.warmup)
+    ols = []
+    for p, i in lattices:
+        o = oracle.Lattice(p)
+        o.init_shape(i)
+        ols.append(o)
+    for o in ols:
+        o.step(args.warmup)
     t = time.perf_counter()
-    o.step(args.steps)
+    for _ in range(args.steps):
+        for o in ols:
+            o.step(1)
     dt = time.perf_counter() - t
-    n = edge ** 3
+    n = sum(p["nx"] * p["ny"] * p["nz"] for p, _ in lattices)
     value = n * args.steps / dt / 1e6
-    sample = (f"FP64 oracle (plain C, OpenMP) on a {edge}^3 crop of the {args.workload} workload "
-              f"(same geometry and parameters, radius scaled), one oracle step per benchmark step")
     out = {"metric": "MLUPS", "value": value, "unit": "MLUPS", "impl": "reference", "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": describe(args.workload, params, args.storage), "sample_lattice": f"{edge}^3"},
+           "config": {"workload": label, "sample_sites": n},
            "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
@@ -556,9 +606,7 @@ def run_ensemble(args):
            # the 64 lattices are split over the ranks: the total work is fixed as N grows
            "scaling": "strong" if world > 1 else "weak",
            "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
-           "config": {"workload": "ensemble_64: 64 two-component D3Q19 Shan-Chen lattices, edges "
-                                  "exp(U(ln 32, ln 96)) per axis, even = planar film on a wall, odd = droplet, "
-                                  "g ~ U(3.2, 3.8), tau ~ U(0.8, 1.2), master seed 3",
+           "config": {"workload": ENSEMBLE_DESC,
                       "sites": n_all, "lattices_per_gpu": len(members), "l2": "inputs larger than L2 (no flush)",
                       "tile": sc.tile_list()[tile - 1], "zchunk": zc, "items": info["items"],
                       "parallelism": "one persistent launch per step over all members"
@@ -672,9 +720,7 @@ def run_serve(args):
            # one stream dispatched over the ranks: the total work is fixed as N grows
            "scaling": "strong" if world > 1 else "weak", "vs_baseline": None,
            "dtype": storage, "data": "synthetic",
-           "config": {"workload": f"serve: {args.requests} requests, Poisson {args.rate}/s, cubic lattices edge "
-                                  f"exp(U(ln 32, ln 160)), 2000-20000 steps, films and droplets, g ~ U(3.2, 3.8), "
-                                  f"tau ~ U(0.8, 1.2), {storage} offsets, master seed 4",
+           "config": {"workload": serve_desc(args, storage),
                       "site_updates": work, "arena_bytes": arena, "diag_every": 100,
                       "l2": "inputs larger than L2 (no flush)",
                       "parallelism": f"requests dispatched round-robin over {world} ranks, no data exchange"
