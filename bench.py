@@ -353,6 +353,11 @@ def run_ours(args):
     params, init = workload(args.workload, args.storage, args.tile, args.zchunk, args.layout)
     n = params["nx"] * params["ny"] * params["nz"]
     aa = args.layout == "aa"
+    need, free = sc.required_bytes(params), torch.cuda.mem_get_info()[0]
+    if need > free:
+        raise SystemExit(f"{args.workload} with {args.storage} populations and the {args.layout} layout needs "
+                         f"{need / 1e9:.1f} GB of device memory, {free / 1e9:.1f} GB are free: use --layout aa "
+                         f"(one population lattice) or --storage f16")
     lat = sc.Lattice(params)
     lat.init(init)
     tuned = None
