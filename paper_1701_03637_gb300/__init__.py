@@ -79,7 +79,11 @@ def _current_stream_handle(device):
 class Lattice:
     """One lattice on the current CUDA device.
 
-    ``params``: dict with the fields of ``sc_params`` (``nx, ny, nz`` required).
+    ``params``: dict with the fields of ``sc_params`` (``nx, ny, nz`` required);
+    ``storage`` may be "f32", "f16", "bf16" or "f16s", ``geometry`` "periodic",
+    "planar" or "sphere", ``layout`` "two" (two population lattices) or "aa" (one
+    updated in place, half the memory, the same bits); ``G`` is the cross coupling
+    of Eq. (3), ``G_rr``/``G_bb`` optional self couplings (the multiphase model).
     Device memory is a torch uint8 tensor lent to ``sc_lbm_create_ext`` (it must
     outlive the handle, which this object guarantees); the stream is torch's
     current stream unless ``stream`` (a ``torch.cuda.Stream``) is given.
