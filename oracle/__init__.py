@@ -62,35 +62,56 @@ class Diag(C.Structure):
                 ("interface_z", C.c_double), ("radius", C.c_double), ("droplet_sites", C.c_int64)]
 
 
+def configure(L):
+    """Declare the C signatures on a loaded oracle library (the built one, or a
+    variant compiled from a modified copy of the source by a test)."""
+    dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+    L.orc_create.argtypes = [C.POINTER(Params), C.POINTER(C.c_void_p)]
+    L.orc_destroy.argtypes = [C.c_void_p]
+    L.orc_set_threads.argtypes = [C.c_int]
+    L.orc_threads.restype = C.c_int
+    L.orc_init_shape.argtypes = [C.c_void_p, C.POINTER(Init)]
+    L.orc_init_fields.argtypes = [C.c_void_p, dp, dp]
+    L.orc_set_populations.argtypes = [C.c_void_p, dp]
+    L.orc_get_populations.argtypes = [C.c_void_p, dp]
+    L.orc_step.argtypes = [C.c_void_p, C.c_int64]
+    L.orc_fields.argtypes = [C.c_void_p, dp, dp]
+    L.orc_profile.argtypes = [C.c_void_p, dp]
+    L.orc_diag_get.argtypes = [C.c_void_p, C.POINTER(Diag)]
+    L.orc_flux_field.argtypes = [C.c_void_p, dp]
+    L.orc_site_class.argtypes = [C.c_void_p, np.ctypeslib.ndpointer(dtype=np.int8, flags="C_CONTIGUOUS")]
+    L.orc_lattice_tables.argtypes = [np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS"), dp,
+                                     np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")]
+    L.orc_feq.argtypes = [C.c_double, dp, dp]
+    L.orc_splitmix64.argtypes = [C.c_uint64, C.c_uint64]
+    L.orc_splitmix64.restype = C.c_uint64
+    L.orc_uniform.argtypes = [C.c_uint64, C.c_uint64]
+    L.orc_uniform.restype = C.c_double
+    return L
+
+
+def compile_variant(src_text: str, out_dir: str, name: str = "variant") -> C.CDLL:
+    """Compile source text with the oracle's flags into out_dir and load it. Used by
+    the mutation tests, which plant a mistake in a copy of sc_oracle.c and check
+    that the pins catch it; the built oracle is untouched."""
+    src = os.path.join(out_dir, f"{name}.c")
+    with open(src, "w") as fh:
+        fh.write(src_text)
+    for h in ("sc_oracle.h",):
+        with open(os.path.join(HERE, h)) as fi, open(os.path.join(out_dir, h), "w") as fo:
+            fo.write(fi.read())
+    so = os.path.join(out_dir, f"lib{name}.so")
+    subprocess.check_call(["gcc", "-O1", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared", "-fno-fast-math",
+                           "-ffp-contract=off", src, "-o", so, "-lm"])
+    return configure(C.CDLL(so))
+
+
 def lib():
     global _lib
     with _lock:
         if _lib is None:
             build()
-            L = C.CDLL(LIB_PATH)
-            dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
-            L.orc_create.argtypes = [C.POINTER(Params), C.POINTER(C.c_void_p)]
-            L.orc_destroy.argtypes = [C.c_void_p]
-            L.orc_set_threads.argtypes = [C.c_int]
-            L.orc_threads.restype = C.c_int
-            L.orc_init_shape.argtypes = [C.c_void_p, C.POINTER(Init)]
-            L.orc_init_fields.argtypes = [C.c_void_p, dp, dp]
-            L.orc_set_populations.argtypes = [C.c_void_p, dp]
-            L.orc_get_populations.argtypes = [C.c_void_p, dp]
-            L.orc_step.argtypes = [C.c_void_p, C.c_int64]
-            L.orc_fields.argtypes = [C.c_void_p, dp, dp]
-            L.orc_profile.argtypes = [C.c_void_p, dp]
-            L.orc_diag_get.argtypes = [C.c_void_p, C.POINTER(Diag)]
-            L.orc_flux_field.argtypes = [C.c_void_p, dp]
-            L.orc_site_class.argtypes = [C.c_void_p, np.ctypeslib.ndpointer(dtype=np.int8, flags="C_CONTIGUOUS")]
-            L.orc_lattice_tables.argtypes = [np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS"), dp,
-                                             np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")]
-            L.orc_feq.argtypes = [C.c_double, dp, dp]
-            L.orc_splitmix64.argtypes = [C.c_uint64, C.c_uint64]
-            L.orc_splitmix64.restype = C.c_uint64
-            L.orc_uniform.argtypes = [C.c_uint64, C.c_uint64]
-            L.orc_uniform.restype = C.c_double
-            _lib = L
+            _lib = configure(C.CDLL(LIB_PATH))
     return _lib
 
 
@@ -134,7 +155,8 @@ _INIT_DEFAULTS = dict(shape=0, film_z=0, cx=0.0, cy=0.0, cz=0.0, radius=0.0, rho
 class Lattice:
     """One FP64 lattice. ``params`` is a dict with the fields of ``Params``."""
 
-    def __init__(self, params: dict):
+    def __init__(self, params: dict, library=None):
+        self._L = library if library is not None else lib()
         p = dict(_PARAM_DEFAULTS)
         p.update({k: v for k, v in params.items() if k in dict(Params._fields_)})
         self.params = p
@@ -142,7 +164,7 @@ class Lattice:
         self.n = p["nx"] * p["ny"] * p["nz"]
         self._p = Params(**p)
         h = C.c_void_p()
-        rc = lib().orc_create(C.byref(self._p), C.byref(h))
+        rc = self._L.orc_create(C.byref(self._p), C.byref(h))
         if rc != 0:
             raise ValueError(f"oracle: invalid parameters ({rc})")
         self._h = h
@@ -150,54 +172,54 @@ class Lattice:
     def __del__(self):
         h = getattr(self, "_h", None)
         if h is not None and h.value:
-            lib().orc_destroy(h)
+            self._L.orc_destroy(h)
             self._h = None
 
     def init_shape(self, init: dict) -> None:
         i = dict(_INIT_DEFAULTS)
         i.update({k: v for k, v in init.items() if k in dict(Init._fields_)})
-        rc = lib().orc_init_shape(self._h, C.byref(Init(**i)))
+        rc = self._L.orc_init_shape(self._h, C.byref(Init(**i)))
         if rc != 0:
             raise MemoryError("oracle init failed")
 
     def init_fields(self, rho_r: np.ndarray, rho_b: np.ndarray) -> None:
-        lib().orc_init_fields(self._h, np.ascontiguousarray(rho_r, np.float64).ravel(),
+        self._L.orc_init_fields(self._h, np.ascontiguousarray(rho_r, np.float64).ravel(),
                               np.ascontiguousarray(rho_b, np.float64).ravel())
 
     def set_populations(self, f: np.ndarray) -> None:
         f = np.ascontiguousarray(f, np.float64).reshape(2 * Q * self.n)
-        lib().orc_set_populations(self._h, f)
+        self._L.orc_set_populations(self._h, f)
 
     def populations(self) -> np.ndarray:
         out = np.zeros(2 * Q * self.n, np.float64)
-        lib().orc_get_populations(self._h, out)
+        self._L.orc_get_populations(self._h, out)
         return out.reshape(2, Q, *self.shape)
 
     def step(self, n: int = 1) -> None:
-        lib().orc_step(self._h, int(n))
+        self._L.orc_step(self._h, int(n))
 
     def fields(self):
         rr = np.zeros(self.n, np.float64)
         rb = np.zeros(self.n, np.float64)
-        lib().orc_fields(self._h, rr, rb)
+        self._L.orc_fields(self._h, rr, rb)
         return rr.reshape(self.shape), rb.reshape(self.shape)
 
     def profile(self) -> np.ndarray:
         out = np.zeros(self.params["nz"], np.float64)
-        lib().orc_profile(self._h, out)
+        self._L.orc_profile(self._h, out)
         return out
 
     def diagnostics(self) -> dict:
         d = Diag()
-        lib().orc_diag_get(self._h, C.byref(d))
+        self._L.orc_diag_get(self._h, C.byref(d))
         return {k: getattr(d, k) for k, _ in Diag._fields_}
 
     def flux_field(self) -> np.ndarray:
         out = np.zeros(3 * self.n, np.float64)
-        lib().orc_flux_field(self._h, out)
+        self._L.orc_flux_field(self._h, out)
         return out.reshape(3, *self.shape)
 
     def site_class(self) -> np.ndarray:
         out = np.zeros(self.n, np.int8)
-        lib().orc_site_class(self._h, out)
+        self._L.orc_site_class(self._h, out)
         return out.reshape(self.shape)
