@@ -190,6 +190,16 @@ int sc_lbm_diagnostics(sc_lbm* h, sc_diag* out);
 /* phi(z) = mean over non-solid (x, y) of rho^r - rho^b, nz doubles (NaN for solid planes). */
 int sc_lbm_profile(sc_lbm* h, double* phi_host);
 
+/* Relative flux of component r of Sec. III A, j^r = rho^r (U^r - U) with the velocities
+   of Eq. (velw): U = (m^r + m^b + (F^r + F^b) / 2) / rho and U^r = (m^r + F^r +
+   rho^r u') / (2 rho^r), rho = rho^r + rho^b, u' = (m^r + m^b) / rho, F^c the force of
+   Eq. (3); the paper states these for tau = 1, so the call requires tau_r = tau_b = 1
+   (SC_EINVAL otherwise). Evaluated on the device in FP64 from the canonical populations
+   (0 at sink and solid sites) and averaged over each plane's nx * ny sites:
+   j_host[d * nz + z] (d = 0, 1, 2 for x, y, z; 3 * nz caller-owned doubles).
+   Synchronous. */
+int sc_lbm_flux_profile(sc_lbm* h, double* j_host);
+
 /* Diagnostics for callers that cannot allocate device memory (for instance code
    running under an allocator they do not control, or inside a process whose
    memory budget is fixed up front). The paper has no counterpart: this is the
@@ -200,8 +210,11 @@ int sc_lbm_profile(sc_lbm* h, double* phi_host);
    synchronize. It writes 8 doubles to out_dev (caller-owned device memory), in
    order: mass_r, mass_b, evaporated_mass, flux_last, interface_z, radius,
    droplet_sites, status; they are ready when the handle's stream reaches this
-   point. Returns SC_EINVAL when nz * (plane splits) * 8 exceeds the array (nz
-   beyond about 16000). The first call on a device looks up the array's device
+   point. Returns SC_EINVAL when nz * (plane splits) * 8 exceeds the array's 262144
+   doubles; a lattice is split into max(1, min(ceil(608 / nz), ceil(nx * ny / 1024)))
+   parts per plane, one for every nz >= 608, so this happens exactly when nz > 32768.
+   The first call on a device (and the first after the device's context has been
+   destroyed and recreated, e.g. by cudaDeviceReset) looks up the array's device
    address, so it should come before any stream capture on that device. All calls
    on a device share the array: calls whose work overlaps on the GPU race. */
 int sc_lbm_diagnostics_noalloc(sc_lbm* h, double* out_dev);
@@ -221,6 +234,12 @@ int sc_lbm_launch_info(sc_lbm* h, int32_t* tile_x, int32_t* tile_y, int32_t* zch
    SC_LAYOUT_AA there is no spare buffer and one configuration: it times nothing
    and reports tile 0 and the current planes per CTA. */
 int sc_lbm_tune(sc_lbm* h, int32_t trials, int32_t* tile, int32_t* zchunk);
+/* Kernel launches that sc_lbm_step(h, nsteps) issues with the current configuration
+   (graph replays count each kernel they contain). */
+int sc_lbm_launch_count(sc_lbm* h, int64_t nsteps, int64_t* launches);
+/* Name of the kernel (or kernels) that carries the step in the current configuration,
+   a static string ("" for a NULL handle). */
+const char* sc_lbm_kernel_name(sc_lbm* h);
 /* Bytes one sc_lbm_diagnostics / sc_lbm_profile call copies device-to-host. */
 int sc_lbm_diag_bytes(sc_lbm* h, size_t* bytes);
 /* Number of compiled tile shapes and their extents. */

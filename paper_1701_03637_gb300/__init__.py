@@ -211,6 +211,13 @@ class Lattice:
         check(_lib().sc_lbm_profile(self._h, out.ctypes.data))
         return out
 
+    def flux_profile(self) -> np.ndarray:
+        """Plane means of the relative flux rho^r (U^r - U) of Eqs. (flux) and (velw),
+        shape (3, nz) (x, y, z components), computed on the device (tau = 1)."""
+        out = np.empty(3 * self.nz, np.float64)
+        check(_lib().sc_lbm_flux_profile(self._h, out.ctypes.data))
+        return out.reshape(3, self.nz)
+
     def diag_bytes(self) -> int:
         b = C.c_size_t()
         check(_lib().sc_lbm_diag_bytes(self._h, C.byref(b)))
@@ -222,6 +229,15 @@ class Lattice:
         t, z = C.c_int32(), C.c_int32()
         check(_lib().sc_lbm_tune(self._h, int(trials), C.byref(t), C.byref(z)))
         return dict(tile=t.value, zchunk=z.value)
+
+    def launch_count(self, steps: int) -> int:
+        """Kernel launches that step(steps) issues in the current configuration."""
+        n = C.c_int64()
+        check(_lib().sc_lbm_launch_count(self._h, int(steps), C.byref(n)))
+        return int(n.value)
+
+    def kernel_name(self) -> str:
+        return _lib().sc_lbm_kernel_name(self._h).decode()
 
     def launch_info(self) -> dict:
         tx, ty, zc, n, st = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int64(), C.c_int32()

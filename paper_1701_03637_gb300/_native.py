@@ -105,11 +105,14 @@ _SIGS = {
     "sc_lbm_set_counters": (C.c_int, [_VP, C.c_int64, C.c_double]),
     "sc_lbm_diagnostics": (C.c_int, [_VP, C.POINTER(Diag)]),
     "sc_lbm_profile": (C.c_int, [_VP, _VP]),
+    "sc_lbm_flux_profile": (C.c_int, [_VP, _VP]),
     "sc_lbm_diag_bytes": (C.c_int, [_VP, C.POINTER(C.c_size_t)]),
     "sc_lbm_diagnostics_noalloc": (C.c_int, [_VP, _VP]),
     "sc_lbm_launch_info": (C.c_int, [_VP, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                      C.POINTER(C.c_int64), C.POINTER(C.c_int32)]),
     "sc_lbm_tune": (C.c_int, [_VP, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "sc_lbm_launch_count": (C.c_int, [_VP, C.c_int64, C.POINTER(C.c_int64)]),
+    "sc_lbm_kernel_name": (C.c_char_p, [_VP]),
     "sc_batch_create": (C.c_int, [C.c_size_t, C.c_int32, _VP, C.POINTER(_VP)]),
     "sc_batch_destroy": (None, [_VP]),
     "sc_batch_add": (C.c_int, [_VP, C.POINTER(Params), C.POINTER(C.c_int32), C.POINTER(_VP)]),

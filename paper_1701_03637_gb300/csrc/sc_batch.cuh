@@ -72,11 +72,9 @@ __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 1 ? 512 / (TX * T
     t.run(zb, ze, (kc & 1) != 0);
     if (ls.L.geometry != 0) {
       const double e = t.block_evap();
-      if (threadIdx.x == 0 && !trial) {
-        // a slot per item; a member with more items than slots shares them atomically
-        if (w.y < ls.nslots) ls.evap[w.y] += e;
-        else atomicAdd(&ls.evap[w.y % ls.nslots], e);
-      }
+      // a slot per item (batch_build checks that every member has a slot for each
+      // of its items), so no two CTAs of a launch add to the same slot
+      if (threadIdx.x == 0 && !trial) ls.evap[w.y] += e;
     }
   }
 }
@@ -228,8 +226,9 @@ void batch_drop_graph(sc_batch* b) {
 }
 
 // Items of one member for the batch's tile and target chunk length: cols x nch,
-// with nch near nz / zchunk and, where possible, no more items than the
-// member's evaporated-mass slots.
+// with nch near nz / zchunk and no more items than the member's evaporated-mass
+// slots (a lattice has at least one slot per column of the smallest tile, so
+// cols <= nslots for every tile and nch = 1 always fits).
 int member_nch(const sc_lbm* h, int cols, int zchunk) {
   const long long nz = h->p.nz;
   long long nch = std::max(1LL, (nz + zchunk / 2) / std::max(1, zchunk));
@@ -259,6 +258,9 @@ int batch_build(sc_batch* b) {
     s.cols = s.cols_x * ((h->p.ny + kTileY[b->tile] - 1) / kTileY[b->tile]);
     s.nch = member_nch(h, s.cols, b->zchunk);
     s.nslots = (int)h->lay.nslots;
+    if ((long long)s.cols * s.nch > h->lay.nslots)
+      return fail(SC_EINVAL, "member %d has %lld items but %lld evaporated-mass slots", m,
+                  (long long)s.cols * s.nch, h->lay.nslots);
     lats.push_back(s);
     cost.push_back((double)((h->p.nz + s.nch - 1) / s.nch + 2));
   }

@@ -1,6 +1,7 @@
 // sc_lbm: C ABI and launches for the two-component Shan-Chen D3Q19 evaporation
 // step on sm_103a (arXiv:1701.03637, Sec. II). include/sc_lbm.h documents the
 // contract of every entry point.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -289,6 +290,97 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag(const LatDev L, const typ
   }
 }
 
+// ------------------------------------------------------------------ relative flux of Sec. III A
+//
+// j^r = rho^r (U^r - U) of Eqs. (flux) and (velw) (the paper states them for
+// tau = 1): U = (m^r + m^b + (F^r + F^b) / 2) / (rho^r + rho^b) and U^r = (m^r + F^r
+// + rho^r u') / (2 rho^r) with u' = (m^r + m^b) / (rho^r + rho^b) and F^c the force of
+// Eq. (3) (periodic neighbours, Psi = 0 at solid sites, self couplings included),
+// evaluated in FP64 from the canonical populations; 0 at sink and solid sites.
+// Per (plane, split) partial sums of the three components go to `part`.
+
+// FP64 densities of the canonical populations of site (x, y, z); returns its class.
+template <class S>
+__device__ __forceinline__ int canonical_rho(const LatDev& L, const typename S::T* __restrict__ src, int odd, int x,
+                                             int y, int z, double& rr, double& rb, float (&fr)[Q], float (&fb)[Q]) {
+  const int cls = site_class(L, x, y, z);
+  rr = rb = 0.0;
+  if (cls == SOLID) return cls;
+  const PullIdx P(L, x, y, z);
+  arrived<S>(L, src, P, odd, fr, fb);
+  if (cls == SINK) {
+    float a = sum19(fr), b = sum19(fb);
+    sink_densities(L, a, b);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) { fr[i] = rest_pop(i, a); fb[i] = rest_pop(i, b); }
+  }
+#pragma unroll
+  for (int i = 0; i < Q; ++i) { rr += (double)fr[i]; rb += (double)fb[i]; }
+  return cls;
+}
+
+template <class S>
+__global__ void __launch_bounds__(kDiagThreads) k_flux(const LatDev L, const typename S::T* __restrict__ src,
+                                                       int nsplit, double* __restrict__ part, int odd, double G,
+                                                       double g_rr, double g_bb) {
+  const int z = blockIdx.x, k = blockIdx.y;
+  const int nxy = L.nx * L.ny;
+  const int per = (nxy + nsplit - 1) / nsplit;
+  const int b = k * per, e = min(b + per, nxy);
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int q = b + threadIdx.x; q < e; q += blockDim.x) {
+    const int x = q % L.nx, y = q / L.nx;
+    float fr[Q], fb[Q];
+    double rr, rb;
+    if (canonical_rho<S>(L, src, odd, x, y, z, rr, rb, fr, fb) != FLUID) continue;
+    double mr[3] = {0.0, 0.0, 0.0}, mb[3] = {0.0, 0.0, 0.0}, ar[3] = {0.0, 0.0, 0.0}, ab[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      const double e[3] = {(double)dir_x(i), (double)dir_y(i), (double)dir_z(i)};
+#pragma unroll
+      for (int d = 0; d < 3; ++d) { mr[d] += e[d] * (double)fr[i]; mb[d] += e[d] * (double)fb[i]; }
+    }
+    // sum_i w_i Psi(x + e_i) e_i of both components over the 18 neighbours
+#pragma unroll 1
+    for (int i = 1; i < Q; ++i) {
+      const int ex = dir_x(i), ey = dir_y(i), ez = dir_z(i);
+      float gr[Q], gb[Q];
+      double nr, nb;
+      const int cls = canonical_rho<S>(L, src, odd, wrap_near(x + ex, L.nx), wrap_near(y + ey, L.ny),
+                                       wrap_near(z + ez, L.nz), nr, nb, gr, gb);
+      const double pr = cls == SOLID ? 0.0 : 1.0 - exp(-nr), pb = cls == SOLID ? 0.0 : 1.0 - exp(-nb);
+      const double w = wgt_d(i);
+      ar[0] += w * pr * ex; ar[1] += w * pr * ey; ar[2] += w * pr * ez;
+      ab[0] += w * pb * ex; ab[1] += w * pb * ey; ab[2] += w * pb * ez;
+    }
+    const double psr = 1.0 - exp(-rr), psb = 1.0 - exp(-rb), rt = rr + rb;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      double Fr = -psr * G * ab[d], Fb = -psb * G * ar[d];
+      if (g_rr != 0.0) Fr += -psr * g_rr * ar[d];
+      if (g_bb != 0.0) Fb += -psb * g_bb * ab[d];
+      if (rr > 0.0 && rt > 0.0) {
+        const double U = (mr[d] + mb[d] + 0.5 * (Fr + Fb)) / rt;
+        const double Ur = (mr[d] + Fr + rr * (mr[d] + mb[d]) / rt) / (2.0 * rr);
+        acc[d] += rr * (Ur - U);
+      }
+    }
+  }
+  __shared__ double red[kDiagThreads / 32][3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    double v = acc[d];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][d] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double t = 0.0;
+    for (int w = 0; w < kDiagThreads / 32; ++w) t += red[w][threadIdx.x];
+    part[((long long)z * nsplit + k) * kDiagFields + threadIdx.x] = t;
+  }
+}
+
 // ------------------------------------------------------------------ diagnostics without allocation
 //
 // For callers that cannot allocate device memory: the per-plane partial sums
@@ -532,7 +624,12 @@ Layout make_layout(const sc_params* p) {
   l.units = (long long)l.cols * p->nz;
   l.aa_segs = (p->nx + kAAThreads - 1) / kAAThreads;
   l.aa_units = (long long)l.aa_segs * p->ny * p->nz;
-  l.nslots = std::min(l.aa ? l.aa_units : l.units, kMaxCtas);
+  // evaporated-mass slots: one per CTA of the persistent step (at most kMaxCtas),
+  // and at least one per tile column of the smallest tile, so that a batch, which
+  // books every (tile column, z chunk) item in a slot of its own, never has more
+  // items of this lattice than slots (member_nch in sc_batch.cuh)
+  const long long min_tile_cols = (long long)((p->nx + 7) / 8) * ((p->ny + 3) / 4);
+  l.nslots = std::max(std::min(l.aa ? l.aa_units : l.units, kMaxCtas), min_tile_cols);
   const long long per_plane = (long long)p->nx * p->ny;
   l.diag_nsplit = (int)std::max(1LL, std::min<long long>((4LL * 152 + p->nz - 1) / p->nz, (per_plane + 1023) / 1024));
   const size_t pop = align256((size_t)(2 * Q * l.np * es));
@@ -843,22 +940,70 @@ long long slab_sites(const sc_lbm* h) { return std::max<long long>(1, (2 * h->la
 }  // namespace
 
 namespace {
-std::mutex g_noalloc_mu;
-double* g_noalloc_ptr[128] = {};  // address of g_noalloc_scratch per device ordinal
+// Identity of the calling thread's current CUDA context (0 if the driver cannot
+// say), through driver entry points that the runtime hands out, so the library
+// needs no link against the driver library. A context destroyed by
+// cudaDeviceReset and recreated gets a new identity.
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
 
-// Device address of the file-scope scratch for the current device, looked up once
-// per device (host code may not use the symbol itself as a device pointer).
+unsigned long long current_context_id() {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = (CtxGetCurrentFn)fn;
+    fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = (CtxGetIdFn)fn;
+  });
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
+
+std::mutex g_noalloc_mu;
+struct NoallocAddr {
+  unsigned long long ctx;  // context the address belongs to (0: not looked up)
+  double* ptr;
+};
+NoallocAddr g_noalloc_addr[128] = {};  // per device ordinal
+
+// Device address of the file-scope scratch for the current device (host code may
+// not use the symbol itself as a device pointer). It is looked up on the first
+// call on a device and again whenever the device's context has changed since
+// (after cudaDeviceReset the module, and with it the array, is loaded anew);
+// when no context is current yet, or its identity is unavailable, it is looked
+// up on every call (the lookup itself makes the primary context current).
 int noalloc_scratch(double** out) {
   int dev = 0;
   CK(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 128) return fail(SC_EINVAL, "device ordinal %d out of range", dev);
+  const unsigned long long ctx = current_context_id();
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
+  NoallocAddr& a = g_noalloc_addr[dev];
+  if (ctx == 0 || a.ctx != ctx || !a.ptr) {
     void* p = nullptr;
     CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-    g_noalloc_ptr[dev] = (double*)p;
+    a.ptr = (double*)p;
+    a.ctx = ctx;
   }
-  *out = g_noalloc_ptr[dev];
+  *out = a.ptr;
+  return SC_OK;
+}
+
+template <class S>
+int launch_flux(sc_lbm* h) {
+  dim3 grid(h->p.nz, h->lay.diag_nsplit);
+  k_flux<S><<<grid, kDiagThreads, 0, h->stream>>>(h->L, (const typename S::T*)h->pop(h->cur), h->lay.diag_nsplit,
+                                                  h->diag(), h->odd(), h->p.G, h->p.G_rr, h->p.G_bb);
+  CK(cudaGetLastError());
   return SC_OK;
 }
 
@@ -1153,6 +1298,33 @@ static int run_diag(sc_lbm* h) {
   return SC_OK;
 }
 
+int sc_lbm_flux_profile(sc_lbm* h, double* j) {
+  Range range("sc_lbm_flux_profile");
+  if (!h || !j) return fail(SC_EINVAL, "NULL argument");
+  if (h->p.tau_r != 1.0 || h->p.tau_b != 1.0)
+    return fail(SC_EINVAL, "the relative flux of Eqs. (flux) and (velw) is defined for tau = 1");
+  int rc;
+  switch (h->p.storage) {
+    case SC_STORAGE_F16: rc = launch_flux<StF16>(h); break;
+    case SC_STORAGE_F16_SCALED: rc = launch_flux<StF16S>(h); break;
+    case SC_STORAGE_BF16: rc = launch_flux<StBF16>(h); break;
+    default: rc = launch_flux<StF32>(h);
+  }
+  if (rc) return rc;
+  const int nz = h->p.nz, ns = h->lay.diag_nsplit;
+  const size_t nd = (size_t)nz * ns * kDiagFields;
+  CK(cudaMemcpyAsync(h->h_diag, h->diag(), sizeof(double) * nd, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  const double nxy = (double)h->p.nx * h->p.ny;
+  for (int d = 0; d < 3; ++d)
+    for (int z = 0; z < nz; ++z) {
+      double acc = 0.0;
+      for (int k = 0; k < ns; ++k) acc += h->h_diag[((size_t)z * ns + k) * kDiagFields + d];
+      j[(size_t)d * nz + z] = acc / nxy;
+    }
+  return SC_OK;
+}
+
 int sc_lbm_profile(sc_lbm* h, double* phi) {
   if (!h || !phi) return fail(SC_EINVAL, "NULL argument");
   int rc = run_diag(h);
@@ -1306,6 +1478,19 @@ int sc_lbm_tune(sc_lbm* h, int32_t trials, int32_t* tile, int32_t* zchunk) {
   if (tile) *tile = h->lay.tile + 1;
   if (zchunk) *zchunk = h->zmax;
   return SC_OK;
+}
+
+int sc_lbm_launch_count(sc_lbm* h, int64_t nsteps, int64_t* launches) {
+  if (!h || !launches) return fail(SC_EINVAL, "NULL argument");
+  if (nsteps < 0) return fail(SC_EINVAL, "nsteps must be >= 0");
+  *launches = h->lay.aa ? 2 * nsteps : nsteps;
+  return SC_OK;
+}
+
+const char* sc_lbm_kernel_name(sc_lbm* h) {
+  if (!h) return "";
+  if (h->lay.aa) return "k_aa_psi + k_aa_collide";
+  return h->lay.rows ? "k_step (staged rows)" : "k_step (per-thread pulls)";
 }
 
 int sc_lbm_diag_bytes(sc_lbm* h, size_t* bytes) {

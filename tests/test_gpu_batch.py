@@ -192,3 +192,30 @@ def test_member_matches_the_oracle(sc, oracle_mod):
     orr, ob = o.fields()
     assert np.max(np.abs(gr - orr)) < 1e-4 and np.max(np.abs(gb - ob)) < 1e-4
     b.close()
+
+
+@pytest.mark.parametrize("extent", [(64, 64, 2), (512, 288, 2)])
+def test_thin_wide_member_books_every_item_in_its_own_slot(sc, extent):
+    """A member with more tile columns of the batch's 8x4 tile than work items of
+    its own step (64x64x2), or more than the single-lattice step's CTA cap of 4096
+    (512x288x2): every (column, chunk) item still has an evaporated-mass slot of
+    its own, so the evaporated mass equals the lone run's (to FP64 summation order)
+    and is the same from run to run."""
+    nx, ny, nz = extent
+    p = dict(nx=nx, ny=ny, nz=nz, tau_r=1.0, tau_b=1.0, G=3.6, rho_H=0.01, geometry=1, sink_z0=1, sink_layers=1)
+    i = dict(shape=0, film_z=1, rho_hi=0.7, rho_lo=0.04, noise_amp=1e-3, seed=21)
+    runs = []
+    for _ in range(2):
+        b = sc.Batch(1 << 29)
+        b.configure(tile=4, zchunk=1)  # the 8x4 tile: the most columns
+        _, lat = b.add(p)
+        lat.init(i)
+        b.step(70)
+        runs.append((lat.read_populations(), lat.diagnostics()))
+        b.close()
+    f_ref, d_ref = _alone(sc, p, i, 70)
+    assert d_ref["evaporated_mass"] > 0
+    for f, d in runs:
+        assert np.array_equal(f, f_ref)
+        _same_bookkeeping(d, d_ref)
+    assert runs[0][1] == runs[1][1]

@@ -40,14 +40,18 @@ def _close(a, b, rel):
     return abs(a - b) <= rel * max(1.0, abs(b))
 
 
-@pytest.mark.parametrize("case", ["droplet_sphere_sink", "film_wall_sink", "droplet_sphere_sink_in_place"])
-def test_noalloc_matches_diagnostics_twice(sc, case):
+@pytest.mark.parametrize("case,storage", [("droplet_sphere_sink", "f32"), ("film_wall_sink", "f32"),
+                                          ("droplet_sphere_sink_in_place", "f32"), ("droplet_sphere_sink", "f16"),
+                                          ("droplet_sphere_sink", "f16s"), ("droplet_sphere_sink", "bf16"),
+                                          ("droplet_sphere_sink_in_place", "f16")])
+def test_noalloc_matches_diagnostics_twice(sc, case, storage):
     import torch
     from paper_1701_03637_gb300.workloads import droplet, film_4x4x128
     if case.startswith("droplet_sphere_sink"):
         params, init = droplet(40, 9.0, 11, spherical_sink=True)
     else:
         params, init = film_4x4x128(rho_hi=0.7, rho_lo=0.04, rho_H=0.01)
+    params["storage"] = storage
     if case.endswith("in_place"):
         params["layout"] = "aa"  # 40 steps: even form, 65 steps: odd form
     lat = sc.Lattice(params)
@@ -67,11 +71,19 @@ def test_noalloc_matches_diagnostics_twice(sc, case):
     lat.close()
 
 
-def test_noalloc_rejects_lattices_beyond_its_scratch(sc):
+def test_noalloc_limit_is_nz_32768(sc):
+    """One part per plane for nz >= 608, 8 doubles per part, 262144 doubles of
+    scratch: nz = 32768 fits exactly, nz = 32769 is rejected."""
     import torch
     from paper_1701_03637_gb300 import _native
-    lat = sc.Lattice(dict(nx=2, ny=2, nz=40000))
     out = torch.zeros(8, dtype=torch.float64, device="cuda")
+    ok = sc.Lattice(dict(nx=1, ny=1, nz=32768))
+    ok.init(dict(shape=0, film_z=100, rho_hi=0.7, rho_lo=0.04))
+    got = _noalloc(sc, ok, out)
+    ref = ok.diagnostics()
+    assert _close(got["mass_r"], ref["mass_r"], 1e-12) and got["interface_z"] == ref["interface_z"]
+    ok.close()
+    lat = sc.Lattice(dict(nx=1, ny=1, nz=32769))
     rc = _native.load().sc_lbm_diagnostics_noalloc(lat.handle, C.c_void_p(out.data_ptr()))
     assert rc == -1
     assert b"limit" in _native.load().sc_last_error()
