@@ -195,3 +195,17 @@ def erfc_profile(z, t, D, rho_H):
     """Dirichlet reservoir into an empty half space: rho = rho_H erfc(z / (2 sqrt(D t)))."""
     from scipy.special import erfc
     return rho_H * erfc(np.asarray(z, dtype=np.float64) / (2.0 * math.sqrt(D * t)))
+
+
+def bulk_pressure(rho_r, rho_b, G, G_rr=0.0, G_bb=0.0):
+    """Bulk pressure of the two-component Shan-Chen fluid with Psi = 1 - exp(-rho)
+    (Sec. III C): c_s^2 (rho^r + rho^b) + G c_s^2 Psi^r Psi^b, the force of Eq. (3)
+    expanded with sum_i w_i e_i e_i = c_s^2 I (the paper prints the interaction term
+    with a factor 1/2 that this expansion does not give), plus g^{cc} c_s^2 (Psi^c)^2 / 2
+    for self couplings."""
+    cs2 = 1.0 / 3.0
+    rr = np.asarray(rho_r, np.float64)
+    rb = np.asarray(rho_b, np.float64)
+    pr = psi(rr)
+    pb = psi(rb)
+    return cs2 * (rr + rb) + G * cs2 * pr * pb + 0.5 * cs2 * (G_rr * pr * pr + G_bb * pb * pb)

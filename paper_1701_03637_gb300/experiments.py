@@ -1,11 +1,14 @@
 """Experiments of arXiv:1701.03637 Sec. III run on the library's step.
 
-These drive the CUDA path through the public API and measure what the paper
-compares with its laws: the surface tension from the Laplace law (pressure
-jump across a droplet against 1/R, the sink closed), the radius of an
-evaporating droplet with the spherical sink r >= R_H over time (Sec. III C),
-and the interface position of an evaporating planar film (Sec. III B).
-They only read fields and diagnostics; every time step runs in the library.
+These drive the CUDA path through the public API and record what the paper
+compares with its laws: the densities inside and outside droplets of several
+radii for the Laplace law (the sink closed), the radius of an evaporating
+droplet with the spherical sink r >= R_H over time (Sec. III C), the interface
+position of an evaporating planar film (Sec. III B), and the profiles and
+relative flux of the diffusion column (Sec. III A). They only read fields,
+diagnostics and the device-computed flux; every time step and every evaluation
+of the method's formulas runs in the library. The equation of state that turns
+densities into a pressure jump is the caller's (`pressure` arguments).
 """
 from __future__ import annotations
 
@@ -14,19 +17,6 @@ import math
 import numpy as np
 
 from . import Lattice
-
-CS2 = 1.0 / 3.0
-
-
-def bulk_pressure(rho_r, rho_b, G, G_rr=0.0, G_bb=0.0):
-    """Bulk pressure of the two-component Shan-Chen fluid with Psi = 1 - exp(-rho):
-    c_s^2 (rho^r + rho^b) + G c_s^2 Psi^r Psi^b (the force of Eq. (3) with
-    sum_i w_i e_i e_i = c_s^2 I), plus g^{cc} c_s^2 (Psi^c)^2 / 2 for self couplings."""
-    pr = 1.0 - np.exp(-np.asarray(rho_r, np.float64))
-    pb = 1.0 - np.exp(-np.asarray(rho_b, np.float64))
-    return (CS2 * (np.asarray(rho_r, np.float64) + rho_b) + G * CS2 * pr * pb
-            + 0.5 * CS2 * (G_rr * pr * pr + G_bb * pb * pb))
-
 
 def _droplet_params(n, G, tau, geometry=0, R_H=0.0, rho_H=0.03, storage="f32"):
     c = n / 2.0
@@ -41,11 +31,13 @@ def _init(n, R, rho, seed):
     return dict(shape=1, cx=c, cy=c, cz=c, radius=R, rho_hi=rho[0], rho_lo=rho[1], noise_amp=1e-4, seed=seed)
 
 
-def surface_tension(radii=(8.0, 12.0, 16.0), margin=12, steps=4000, G=3.6, tau=1.0, rho=(0.7, 0.04), seed=5):
+def surface_tension(pressure, radii=(8.0, 12.0, 16.0), margin=12, steps=4000, G=3.6, tau=1.0, rho=(0.7, 0.04),
+                    seed=5):
     """Laplace test with the sink closed: for each initial radius a droplet in a
     periodic box of edge 2 R + 2 margin equilibrates for `steps` steps; the
-    pressure jump between the centre and the box corner is fitted against 1/R
-    (R from the droplet volume). Returns gamma = slope / 2 and the fit data."""
+    pressure jump between the centre and the box corner, pressure(rho^r, rho^b, G)
+    of the caller's equation of state, is fitted against 1/R (R from the droplet
+    volume). Returns gamma = slope / 2 and the fit data."""
     inv_r, dp = [], []
     for R0 in radii:
         n = int(2 * R0 + 2 * margin)
@@ -57,17 +49,18 @@ def surface_tension(radii=(8.0, 12.0, 16.0), margin=12, steps=4000, G=3.6, tau=1
         lat.close()
         m = n // 2
         inv_r.append(1.0 / d["radius"])
-        dp.append(float(bulk_pressure(rr[m, m, m], rb[m, m, m], G) - bulk_pressure(rr[0, 0, 0], rb[0, 0, 0], G)))
+        dp.append(float(pressure(rr[m, m, m], rb[m, m, m], G) - pressure(rr[0, 0, 0], rb[0, 0, 0], G)))
     slope, icpt = np.polyfit(inv_r, dp, 1)
     return dict(gamma=slope / 2.0, intercept=icpt, inv_radius=inv_r, pressure_jump=dp)
 
 
-def single_component_laplace(g, rho_l, rho_g, radii=(8.0, 12.0, 16.0), margin=12, steps=3000):
+def single_component_laplace(pressure, g, rho_l, rho_g, radii=(8.0, 12.0, 16.0), margin=12, steps=3000):
     """Laplace test of the multiphase pseudopotential model (component b absent,
     self coupling g^{rr} = g, no cross coupling): a liquid droplet (rho_l) in its
     vapour (rho_g) in a periodic box of edge 2 R + 2 margin settles for `steps`
     steps; R is the radius of the volume where rho > (rho_l + rho_g) / 2. Returns
-    gamma = slope / 2 of the pressure jump against 1/R and the fit data."""
+    gamma = slope / 2 of the jump of pressure(rho^r, 0, 0, G_rr=g) (the caller's
+    equation of state) against 1/R and the fit data."""
     inv_r, dp = [], []
     for R0 in radii:
         n = int(2 * R0 + 2 * margin)
@@ -82,7 +75,7 @@ def single_component_laplace(g, rho_l, rho_g, radii=(8.0, 12.0, 16.0), margin=12
         m = n // 2
         vol = float(np.count_nonzero(rr > 0.5 * (rho_l + rho_g)))
         inv_r.append(1.0 / equivalent_radius(vol))
-        dp.append(float(bulk_pressure(rr[m, m, m], 0.0, 0.0, G_rr=g) - bulk_pressure(rr[0, 0, 0], 0.0, 0.0, G_rr=g)))
+        dp.append(float(pressure(rr[m, m, m], 0.0, 0.0, G_rr=g) - pressure(rr[0, 0, 0], 0.0, 0.0, G_rr=g)))
     slope, icpt = np.polyfit(inv_r, dp, 1)
     return dict(gamma=slope / 2.0, intercept=icpt, inv_radius=inv_r, pressure_jump=dp)
 
@@ -181,58 +174,24 @@ def evaporating_film(nz=128, film_z=32, nxy=4, rho=(0.70, 0.04), rho_H=0.02, G=3
                 rho_ma=rho_ma, rho_mi=rho_mi, rho_b_vap=rho_b_vap, rho_H=rho_H, G=G)
 
 
-def paper_flux_z(f, c, w, G):
-    """z flux of component r relative to the mixture, j^r = rho^r (U^r - U), with
-    the velocities of Eq. (velw) at tau = 1: U = (m^r + m^b + (F^r + F^b) / 2) /
-    (rho^r + rho^b) and U^r = (m^r + F^r + rho^r u') / (2 rho^r), u' the common
-    velocity and F^c = -g Psi^c(x) sum_i w_i Psi^cbar(x + e_i) e_i (Eq. (3),
-    periodic neighbours; solid sites have rho = Psi = 0; the paper's cross coupling
-    only). f: canonical populations [2][19][z][y][x] (FP64); c, w: the library's
-    direction table. Equal to the oracle's evaluation to 1e-14
-    (tests/test_flux_definition.py)."""
-    rho = f.sum(axis=1)
-    m = np.tensordot(c.astype(np.float64).T, f, axes=([1], [1]))  # [3][2][z][y][x]
-    psi = -np.expm1(-rho)
-    acc = np.zeros((2, 3) + rho.shape[1:])
-    for i in range(1, len(w)):
-        e = c[i]
-        for cc in (0, 1):
-            pn = np.roll(psi[1 - cc], shift=(-int(e[2]), -int(e[1]), -int(e[0])), axis=(0, 1, 2))
-            for d in range(3):
-                if e[d]:
-                    acc[cc, d] += w[i] * pn * e[d]
-    F = -G * psi[:, None] * acc  # [2][3][...]
-    rr, rb = rho[0], rho[1]
-    rt = np.maximum(rr + rb, 1e-300)
-    up = (m[2, 0] + m[2, 1]) / rt  # tau_r = tau_b: the common velocity is the mixture momentum / mass
-    U = (m[2, 0] + m[2, 1] + 0.5 * (F[0, 2] + F[1, 2])) / rt
-    with np.errstate(divide="ignore", invalid="ignore"):
-        Ur = np.where(rr > 0, (m[2, 0] + F[0, 2] + rr * up) / (2.0 * rr), 0.0)
-    return np.where(rr > 0, rr * (Ur - U), 0.0)
-
-
 def fick_column(nz=128, nxy=4, rho_cbar=0.7, rho_H=0.001, G=3.6, tau=1.0, times=(3000, 10000), storage="f32"):
     """The diffusion experiment of Sec. III A: a column of the other component
     (rho^b = rho_cbar, rho^r = 0) between the evaporation boundary z = 0, which
     holds rho^r = rho_H, and a wall of thickness 2 at the far end. Returns, at each
     time, the xy-mean profiles of rho^r and rho^b and the z flux of r relative to
-    the mixture, rho^r (U^r - U) of Eqs. (flux) and (velw) (tau = 1), from the
-    canonical populations."""
+    the mixture, rho^r (U^r - U) of Eqs. (flux) and (velw) (tau = 1), evaluated on
+    the device (sc_lbm_flux_profile)."""
     p = dict(nx=nxy, ny=nxy, nz=nz, tau_r=tau, tau_b=tau, G=G, rho_H=rho_H, geometry=1, sink_z0=0, sink_layers=1,
              wall_z0=nz - 2, wall_thickness=2, storage=storage)
     lat = Lattice(p)
     lat.init_fields(np.zeros((nz, nxy, nxy), np.float32), np.full((nz, nxy, nxy), rho_cbar, np.float32))
-    from . import lattice_directions
-    c, w = lattice_directions()
     out = []
     done = 0
     for T in times:
         lat.step(T - done)
         done = T
-        f = lat.read_populations()  # [2][19][z][y][x]
-        rho = f.sum(axis=1)
-        j = paper_flux_z(f, c, w, G)
-        out.append(dict(t=T, rho_r=rho[0].mean(axis=(1, 2)), rho_b=rho[1].mean(axis=(1, 2)),
-                        flux=j.mean(axis=(1, 2))))
+        rr, rb = lat.read_fields()
+        out.append(dict(t=T, rho_r=rr.astype(np.float64).mean(axis=(1, 2)), rho_b=rb.astype(np.float64).mean(axis=(1, 2)),
+                        flux=lat.flux_profile()[2]))
     lat.close()
     return out

@@ -35,7 +35,7 @@ def test_droplet_radius_follows_the_laplace_corrected_law(sc):
     from tests.droplet_law import law_dR as _law_dR
     from oracle import analytic as A
     from paper_1701_03637_gb300 import experiments as X
-    lap = X.surface_tension(radii=(8.0, 12.0, 16.0), steps=4000)
+    lap = X.surface_tension(A.bulk_pressure, radii=(8.0, 12.0, 16.0), steps=4000)
     gamma = lap["gamma"]
     assert gamma > 0 and abs(lap["intercept"]) < 0.05 * 2 * gamma * max(lap["inv_radius"])
     run = X.evaporating_droplet(96, 20.0, rho_H=0.03, equilibrate=2000, steps=80000, every=1000)

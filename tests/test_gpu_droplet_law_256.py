@@ -17,6 +17,7 @@ import os
 import numpy as np
 import pytest
 
+from oracle import analytic as A
 from tests.results import save
 
 pytestmark = [pytest.mark.gpu,
@@ -40,7 +41,7 @@ def sc():
 @pytest.fixture(scope="module")
 def gamma(sc):
     from paper_1701_03637_gb300 import experiments as X
-    lap = X.surface_tension(radii=(8.0, 12.0, 16.0), steps=4000, rho=(0.70, 0.04))
+    lap = X.surface_tension(A.bulk_pressure, radii=(8.0, 12.0, 16.0), steps=4000, rho=(0.70, 0.04))
     assert lap["gamma"] > 0
     return lap["gamma"]
 

@@ -5,6 +5,8 @@ mechanical-stability condition, and its droplets obey the Laplace law."""
 import numpy as np
 import pytest
 
+from oracle import analytic as A
+
 pytestmark = pytest.mark.gpu
 
 
@@ -72,7 +74,7 @@ def test_single_component_droplets_obey_laplace(sc):
     from paper_1701_03637_gb300 import experiments as X
     from tests.sc_eos import sc_coexistence
     rg, rl = sc_coexistence(-5.0)
-    lap = X.single_component_laplace(-5.0, rl, rg, radii=(10.0, 14.0, 18.0), steps=4000)
+    lap = X.single_component_laplace(A.bulk_pressure, -5.0, rl, rg, radii=(10.0, 14.0, 18.0), steps=4000)
     print(lap)
     dp = np.asarray(lap["pressure_jump"])
     assert lap["gamma"] > 0 and np.all(dp > 0)
