@@ -1,17 +1,20 @@
 #!/usr/bin/env python
 """Benchmark of the fused two-component Shan-Chen D3Q19 evaporation step.
 
-One benchmark step = one lattice time step of the workload: one fused launch
-with two population lattices, two launches with one lattice updated in place
-(--layout aa).
-Default workload: the 128^3 floating droplet (radius 24, centred; sinks at the
-z-boundary planes z = 127 and z = 0; tau = 1, G = 3.6, rho_H = 0.03; FP32
-populations, two-lattice pull layout; seeded +-1e-4 noise). Its populations
-(2 x 319 MB) exceed the 129 MB L2, so no flush is needed between steps.
+One benchmark step = one lattice time step of the workload.
+Default workload: the 512^3 floating droplet (radius 96, centred; sinks at the
+z-boundary planes z = 511 and z = 0; tau = 1, G = 3.6, rho_H = 0.03; seeded
++-1e-4 noise) with FP32 populations on one lattice updated in place (the AA
+pattern), the large-droplet configuration of the precision study; its 20 GB of
+populations exceed the 129 MB L2 many times, so no flush is needed between steps.
+The same lattice is also timed with FP16 and BF16 offset storage
+(`storage_variants`).
 
 Metric: MLUPS (million site updates per second, both components per update).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload droplet_512|droplet_128|droplet_1024|film_4x4x128|ensemble_64|serve]
+                    [--layout two|aa] [--storage f32|f16|bf16|f16s]
 
 Under torchrun each rank advances its own copy of the lattice (independent
 problems, no data exchange): weak scaling, value = all ranks' site updates /
@@ -37,27 +40,40 @@ BYTES_PER_SITE = {"f32": 304, "f16": 152, "bf16": 152, "f16s": 152}  # read + wr
 # populations and writes (Psi^r, Psi^b) in FP32, its collision reads them again
 # with Psi and writes them back
 AA_BYTES_PER_SITE = {k: 3 * v // 2 + 16 for k, v in BYTES_PER_SITE.items()}
-PROFILE_FILE = os.path.join(ROOT, "profiles", "k_step_droplet_128.md")
+PROFILE_DIR = os.path.join(ROOT, "profiles")
+L2_BYTES = 129e6  # GB300 L2
+# population layout of each workload unless --layout says otherwise: the droplets
+# of 512^3 and more are the in-place (AA) configuration
+DEFAULT_LAYOUT = {"droplet_512": "aa", "droplet_1024": "aa"}
+# the oracle's sample of a workload too large for it: the 128^3 droplet of the same
+# recipe (radius / box = 0.1875), the crop-equivalent case of the precision study
+ORACLE_CROP_EDGE = 128
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10000)
-    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="droplet_128")
+    ap.add_argument("--workload", default="droplet_512")
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16", "f16s"])
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--zchunk", type=int, default=0)
-    ap.add_argument("--layout", default="two", choices=["two", "aa"],
-                    help="two population lattices, or one updated in place (half the memory)")
+    ap.add_argument("--layout", default=None, choices=["two", "aa"],
+                    help="two population lattices, or one updated in place (half the memory); "
+                         "default: in place for the 512^3 and 1024^3 droplets, two lattices otherwise")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip timing the other storage types on the default workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the automatic kernel configuration")
     ap.add_argument("--requests", type=int, default=40, help="serve workload: requests in the stream")
     ap.add_argument("--rate", type=float, default=20.0, help="serve workload: arrivals per second")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.layout is None:
+        args.layout = DEFAULT_LAYOUT.get(args.workload, "two")
+    return args
 
 
 def workload(name, storage, tile=0, zchunk=0, layout="two"):
@@ -97,26 +113,94 @@ def source_digest():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload_name, storage, tile=None, zchunk=None):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on the
-    current kernel source, this workload and this launch configuration; None otherwise."""
+def profile_fields():
+    """Machine-readable fields ("- key: `value`" lines) of every ncu summary under
+    profiles/, one dict per file."""
+    out = []
     try:
-        lines = open(PROFILE_FILE).read().splitlines()
+        names = sorted(os.listdir(PROFILE_DIR))
     except OSError:
-        return None
-    kv = {}
-    for ln in lines:
-        if ln.startswith("- ") and ":" in ln:
-            k, v = ln[2:].split(":", 1)
-            kv[k.strip()] = v.strip().strip("`")
-    if kv.get("source_digest") != source_digest() or kv.get("workload") != workload_name or kv.get("storage") != storage:
-        return None
-    if tile is not None and (kv.get("tile") != tile or kv.get("zchunk") != str(zchunk)):
-        return None
-    try:
-        return float(kv["dram_bytes_per_launch"])
-    except (KeyError, ValueError):
-        return None
+        return out
+    for name in names:
+        if not name.endswith(".md"):
+            continue
+        kv = {"file": name}
+        try:
+            for ln in open(os.path.join(PROFILE_DIR, name)).read().splitlines():
+                if ln.startswith("- ") and ":" in ln:
+                    k, v = ln[2:].split(":", 1)
+                    kv[k.strip()] = v.strip().strip("`")
+        except OSError:
+            continue
+        out.append(kv)
+    return out
+
+
+def profiled_traffic(workload_name, storage, tile=None, zchunk=None, layout="two"):
+    """DRAM bytes per launch of the dominant kernel from a committed ncu summary, if
+    one was taken on the current kernel source, this workload, storage, layout and
+    launch configuration; None otherwise."""
+    for kv in profile_fields():
+        if "dram_bytes_per_launch" not in kv:
+            continue
+        if kv.get("source_digest") != source_digest() or kv.get("workload") != workload_name:
+            continue
+        if kv.get("storage") != storage or kv.get("layout", "two") != layout:
+            continue
+        if tile is not None and (kv.get("tile") != tile or kv.get("zchunk") != str(zchunk)):
+            continue
+        try:
+            return float(kv["dram_bytes_per_launch"])
+        except ValueError:
+            continue
+    return None
+
+
+def l2_note(pop_bytes):
+    """How the timed steps relate to the L2: the populations the steps stream against
+    its 129 MB."""
+    if pop_bytes > L2_BYTES:
+        return f"inputs larger than L2 (no flush): {pop_bytes / 1e9:.3g} GB of populations against 129 MB"
+    return (f"populations fit in L2 ({pop_bytes / 1e6:.3g} MB < 129 MB): steps run back to back without a "
+            f"flush, a warm-L2 figure")
+
+
+def population_bytes(params, storage, layout):
+    es = 4 if storage == "f32" else 2
+    return params["nx"] * params["ny"] * params["nz"] * 38 * es * (1 if layout == "aa" else 2)
+
+
+def arm_config(args, world):
+    """The `config` of a line, the same for this library's arm and the oracle arm:
+    it names the workload (sizes, storage, layout, how it meets the L2, how ranks
+    share it) and nothing about kernels."""
+    from paper_1701_03637_gb300.workloads import ensemble
+    if args.workload == "ensemble_64":
+        members = ensemble(64, 3, args.storage)
+        sites = sum(p["nx"] * p["ny"] * p["nz"] for p, _ in members)
+        return {"workload": ENSEMBLE_DESC, "sites": sites, "lattices": 64, "storage": args.storage,
+                "layout": "two",
+                "l2": l2_note(sum(population_bytes(p, args.storage, "two") for p, _ in members)),
+                "parallelism": "one persistent launch per step over all members"
+                               + (f"; members split over {world} ranks by size, no data exchange" if world > 1 else "")}
+    if args.workload == "serve":
+        storage = args.storage if args.storage != "f32" else "f16"
+        return {"workload": serve_desc(args, storage), "requests": args.requests, "rate_per_s": args.rate,
+                "storage": storage, "layout": "two", "diag_every": 100,
+                "l2": "resident lattices (up to the arena) stream through L2 each step; no flush",
+                "parallelism": f"requests dispatched round-robin over {world} ranks, no data exchange"
+                               if world > 1 else "one GPU"}
+    params, _ = workload(args.workload, args.storage, args.tile, args.zchunk, args.layout)
+    return workload_config(args, params, world)
+
+
+def workload_config(args, params, world):
+    """The `config` of both arms' lines: what the workload is, nothing about kernels."""
+    return {"workload": describe(args.workload, params, args.storage),
+            "sites": params["nx"] * params["ny"] * params["nz"], "lattices_per_gpu": 1,
+            "storage": args.storage, "layout": args.layout,
+            "l2": l2_note(population_bytes(params, args.storage, args.layout)),
+            "parallelism": f"independent replicas x{world}"}
 
 
 def launch_cfg(lat):
@@ -287,7 +371,7 @@ def reference_lattices(args):
         return [(params, init)], (f"FP64 oracle (plain C, OpenMP) on the full {params['nx']}x{params['ny']}x"
                                   f"{params['nz']} lattice of {name}, one oracle step per benchmark step"), \
             describe(name, params, args.storage)
-    edge = int(max(8, min(params["nx"], round(budget ** (1.0 / 3.0)))))
+    edge = int(max(8, min(params["nx"], ORACLE_CROP_EDGE, round(budget ** (1.0 / 3.0)))))
     scale = edge / params["nx"]
     p, i = droplet(edge, init["radius"] * scale, 1, rho_H=params["rho_H"])
     return [(p, i)], (f"FP64 oracle (plain C, OpenMP) on a {edge}^3 crop of the {name} workload (same geometry "
@@ -302,6 +386,7 @@ def run_reference(args):
     if rank != 0:
         return
     import oracle
+    world = int(os.environ.get("WORLD_SIZE", "1"))
     lattices, sample, label = reference_lattices(args)
     cores = host_cores()
     oracle.set_threads(cores)
@@ -322,10 +407,55 @@ def run_reference(args):
     out = {"metric": "MLUPS", "value": value, "unit": "MLUPS", "impl": "reference", "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": label, "sample_sites": n},
+           "config": arm_config(args, world),
+           "sample_sites": n,
            "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
+
+
+def oracle_sample(args, params, init):
+    """The lattice the CPU baseline times: the workload's own lattice, or for a droplet
+    larger than the crop-equivalent edge the 128^3 droplet of the same recipe (radius /
+    box = 0.1875, same sink geometry and parameters); returns (params, init, words)."""
+    from paper_1701_03637_gb300.workloads import droplet
+    if init["shape"] == 0 or params["nx"] <= ORACLE_CROP_EDGE:
+        return params, init, (f"the full {params['nx']}x{params['ny']}x{params['nz']} lattice of this workload")
+    e = ORACLE_CROP_EDGE
+    p, i = droplet(e, init["radius"] * e / params["nx"], 1, rho_H=params["rho_H"])
+    return p, i, (f"the {e}^3 crop-equivalent droplet of this workload (same recipe: radius {i['radius']:g}, "
+                  f"radius / box 0.1875, same sinks and parameters)")
+
+
+def precision_record():
+    """Error against the FP64 oracle of each storage type on the 128^3 crop-equivalent
+    droplet after 1000 steps, from the committed summary of the precision study
+    (tests/test_gpu_precision.py), or None."""
+    for kv in profile_fields():
+        if kv.get("study") == "precision_droplet_128":
+            rec = {"source": f"profiles/{kv['file']}", "case": kv.get("case")}
+            for st in ("f32", "f16", "bf16", "f16s"):
+                if f"{st}_linf" in kv:
+                    rec[st] = {"density_linf": float(kv[f"{st}_linf"]), "density_l2": float(kv[f"{st}_l2"]),
+                               "radius_error": float(kv[f"{st}_radius_error"])}
+            return rec
+    return None
+
+
+def timed_steps(lat, steps, stream, barrier):
+    """K steps between CUDA events on the launching stream, synchronized and behind a
+    barrier on both sides; milliseconds."""
+    import torch
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    lat.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    return e0.elapsed_time(e1)
 
 
 def run_ours(args):
@@ -361,7 +491,7 @@ def run_ours(args):
     lat = sc.Lattice(params)
     lat.init(init)
     tuned = None
-    if not args.tile and not args.zchunk and not args.no_tune and not aa:
+    if not args.tile and not args.zchunk and not args.no_tune:
         tuned = lat.tune(trials=20)  # untimed; leaves the state unchanged
     stream = torch.cuda.current_stream()
     lat.step(args.warmup)
@@ -372,38 +502,27 @@ def run_ours(args):
         bus = None
     sampler = ClockSampler()
     time.sleep(0.3)
-    barrier()
-    torch.cuda.synchronize()
     t0 = time.time()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    lat.step(args.steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
+    ms = timed_steps(lat, args.steps, stream, barrier)
     t1 = time.time()
     sampler.stop()
-    ms = e0.elapsed_time(e1)
     ms_max = slowest(ms)
     d = lat.diagnostics()
     if d["status"] != 0:
         raise RuntimeError(f"diagnostics status {d['status']} after the timed run")
+    launches = lat.launch_count(args.steps)
 
     value = replica_value(n, args.steps, world, ms_max)
     step_s = ms * 1e-3 / args.steps
     peak, peak_kind = measured_peak_hbm()
     achieved = BYTES_PER_SITE[args.storage] * n / step_s / 1e9
+    info = lat.launch_info()
+    tile_s = f"{info['tile_x']}x{info['tile_y']}"
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": None if aa else profiled_traffic(args.workload, args.storage, *launch_cfg(lat)),
+            "traffic": profiled_traffic(args.workload, args.storage, tile_s, info["zchunk"], args.layout),
             "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
-            "algorithmic_bytes_per_site": BYTES_PER_SITE[args.storage]}
-    if aa:
-        # both launches of the step together, against the method's algorithmic bytes;
-        # the bytes the two launches move are reported beside them
-        roof.update(kernel="k_aa_psi + k_aa_collide (one step)",
-                    implementation_bytes_per_site=AA_BYTES_PER_SITE[args.storage],
-                    implementation_frac=AA_BYTES_PER_SITE[args.storage] * n / step_s / 1e9 / peak)
+            "algorithmic_bytes_per_site": BYTES_PER_SITE[args.storage],
+            "kernel": lat.kernel_name(), "launches_per_step": launches / args.steps}
 
     # end to end through the public API: initial densities from pinned host memory,
     # the steps with FP64 diagnostics read back every 100 steps, final densities to host
@@ -412,6 +531,7 @@ def run_ours(args):
         rr0, rb0 = lat.read_fields()
         h_rr = torch.from_numpy(rr0.reshape(-1).copy()).pin_memory()
         h_rb = torch.from_numpy(rb0.reshape(-1).copy()).pin_memory()
+        del rr0, rb0
         o_rr = torch.empty(n, dtype=torch.float32).pin_memory()
         o_rb = torch.empty(n, dtype=torch.float32).pin_memory()
         diag_every = 100
@@ -438,34 +558,59 @@ def run_ours(args):
                "d2h_bytes_per_step": (8 * n + diag_bytes) / args.steps,
                "includes": "init from pinned host densities, all steps, diagnostics every 100 steps, "
                            "final densities to pinned host"}
+        del h_rr, h_rb, o_rr, o_rb
+
+    # the other storage types on the same workload and layout (the precision study's
+    # three runs), each timed over the same K steps after W warm-up steps
+    variants = None
+    if not args.no_variants and args.workload in DEFAULT_LAYOUT and args.storage == "f32":
+        lat.close()
+        variants = {}
+        for st in ("f16", "bf16"):
+            vp, vi = workload(args.workload, st, 0, 0, args.layout)
+            v = sc.Lattice(vp)
+            v.init(vi)
+            v.tune(trials=5)
+            v.step(args.warmup)
+            vms = slowest(timed_steps(v, args.steps, stream, barrier))
+            vd = v.diagnostics()
+            vval = replica_value(n, args.steps, world, vms)
+            variants[st] = {"value": vval, "unit": "MLUPS", "ms_per_step": vms / args.steps,
+                            "frac": BYTES_PER_SITE[st] * vval / world * 1e6 / 1e9 / peak,
+                            "algorithmic_bytes_per_site": BYTES_PER_SITE[st], "status": vd["status"],
+                            "radius": vd["radius"]}
+            v.close()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = host_cores()
-        rate, steps = oracle_rate(params, init, 12.0, cores)
-        rate1, steps1 = oracle_rate(params, init, 6.0, 1)
+        op, oi, words = oracle_sample(args, params, init)
+        rate, steps = oracle_rate(op, oi, 12.0, cores)
+        rate1, steps1 = oracle_rate(op, oi, 6.0, 1)
         cpu = {"value": rate, "unit": "MLUPS", "cores": cores, "kind": "oracle",
-               "sample": f"FP64 oracle (plain C, OpenMP, {cores} threads) on the full "
-                         f"{params['nx']}x{params['ny']}x{params['nz']} lattice of this workload, "
+               "sample": f"FP64 oracle (plain C, OpenMP, {cores} threads) on {words}, "
                          f"{steps} steps after its initial state",
                "single_thread": {"value": rate1, "unit": "MLUPS", "cores": 1,
                                  "sample": f"the same oracle on one thread, {steps1} steps"}}
 
     if rank == 0:
-        info = lat.launch_info()
         clk = sampler.summary(t0, t1, bus)
         out = {"metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
-               "config": {"workload": describe(args.workload, params, args.storage),
-                          "sites": n, "lattices_per_gpu": 1, "l2": "inputs larger than L2 (no flush)",
-                          "tile": f"{info['tile_x']}x{info['tile_y']}", "zchunk": info["zchunk"],
-                          "ctas": info["ctas"], "staging": info["staging"], "layout": args.layout,
-                          "autotuned": tuned is not None, "parallelism": f"independent replicas x{world}"},
-               "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": (2 if aa else 1) * args.steps,
+               "config": workload_config(args, params, world),
+               "launch": {"tile": tile_s, "zchunk": info["zchunk"], "ctas": info["ctas"],
+                          "staging": info["staging"], "autotuned": tuned is not None},
+               "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                "clocks": clk, "diag": {k: d[k] for k in ("mass_r", "mass_b", "evaporated_mass", "radius")}}
+        if variants is not None:
+            out["storage_variants"] = variants
+        rec = precision_record() if args.workload in DEFAULT_LAYOUT else None
+        if rec is not None:
+            out["error_vs_oracle"] = rec
         print(json.dumps(out))
-    lat.close()
+    if variants is None:
+        lat.close()
     if world > 1:
         dist.destroy_process_group()
 
@@ -611,12 +756,9 @@ def run_ensemble(args):
            # the 64 lattices are split over the ranks: the total work is fixed as N grows
            "scaling": "strong" if world > 1 else "weak",
            "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
-           "config": {"workload": ENSEMBLE_DESC,
-                      "sites": n_all, "lattices_per_gpu": len(members), "l2": "inputs larger than L2 (no flush)",
-                      "tile": sc.tile_list()[tile - 1], "zchunk": zc, "items": info["items"],
-                      "parallelism": "one persistent launch per step over all members"
-                                     + (f"; members split over {world} ranks by size, no data exchange"
-                                        if world > 1 else "")},
+           "config": arm_config(args, world),
+           "launch": {"tile": "%dx%d" % sc.tile_list()[tile - 1], "zchunk": zc, "items": info["items"],
+                      "lattices_per_gpu": len(members)},
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                         "traffic": None, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
                         "algorithmic_bytes_per_site": BYTES_PER_SITE[args.storage]},
@@ -725,11 +867,8 @@ def run_serve(args):
            # one stream dispatched over the ranks: the total work is fixed as N grows
            "scaling": "strong" if world > 1 else "weak", "vs_baseline": None,
            "dtype": storage, "data": "synthetic",
-           "config": {"workload": serve_desc(args, storage),
-                      "site_updates": work, "arena_bytes": arena, "diag_every": 100,
-                      "l2": "inputs larger than L2 (no flush)",
-                      "parallelism": f"requests dispatched round-robin over {world} ranks, no data exchange"
-                                     if world > 1 else "one GPU"},
+           "config": arm_config(args, world),
+           "launch": {"site_updates": work, "arena_bytes": arena},
            "serving": {"batched": uncapped,
                        "batched_site_cap": dict(batched, max_active_sites=cap),
                        "sub_capacity": dict(light_s, rate_per_s=args.rate / 20.0),

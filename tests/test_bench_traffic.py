@@ -1,21 +1,24 @@
-"""The benchmark reports the DRAM traffic of the step kernel from the committed ncu
+"""The benchmark reports the DRAM traffic of the step kernel from a committed ncu
 summary only while that summary describes the kernel being timed: same source
-digest, workload, storage and launch configuration; otherwise null."""
+digest, workload, storage, layout and launch configuration; otherwise null. Its
+`config` is the same for both arms and says truthfully how the workload meets the
+L2."""
 import pytest
 
 
-def _summary(tmp_path, digest, tile="64x4", zchunk="32", workload="droplet_128", storage="f32"):
+def _summary(tmp_path, digest, tile="64x4", zchunk="32", workload="droplet_128", storage="f32", layout=None):
     p = tmp_path / "k_step.md"
+    lay = f"- layout: `{layout}`\n" if layout else ""
     p.write_text(f"""# summary
 
 - workload: `{workload}`
 - storage: `{storage}`
-- tile: `{tile}`
+{lay}- tile: `{tile}`
 - zchunk: `{zchunk}`
 - source_digest: `{digest}`
 - dram_bytes_per_launch: `601070592`
 """)
-    return str(p)
+    return str(tmp_path)
 
 
 @pytest.fixture()
@@ -25,7 +28,7 @@ def bench(monkeypatch):
 
 
 def test_traffic_when_everything_matches(bench, tmp_path, monkeypatch):
-    monkeypatch.setattr(bench, "PROFILE_FILE", _summary(tmp_path, bench.source_digest()))
+    monkeypatch.setattr(bench, "PROFILE_DIR", _summary(tmp_path, bench.source_digest()))
     assert bench.profiled_traffic("droplet_128", "f32", "64x4", 32) == 601070592.0
 
 
@@ -42,10 +45,50 @@ def test_no_traffic_when_anything_differs(bench, tmp_path, monkeypatch, change):
         kw["workload"] = "droplet_512"
     else:
         kw["storage"] = "f16"
-    monkeypatch.setattr(bench, "PROFILE_FILE", _summary(tmp_path, **kw))
+    monkeypatch.setattr(bench, "PROFILE_DIR", _summary(tmp_path, **kw))
     assert bench.profiled_traffic("droplet_128", "f32", "64x4", 32) is None
 
 
 def test_missing_summary_gives_no_traffic(bench, tmp_path, monkeypatch):
-    monkeypatch.setattr(bench, "PROFILE_FILE", str(tmp_path / "absent.md"))
+    monkeypatch.setattr(bench, "PROFILE_DIR", str(tmp_path / "absent"))
     assert bench.profiled_traffic("droplet_128", "f32", "64x4", 32) is None
+
+
+def test_layout_must_match(bench, tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "PROFILE_DIR", _summary(tmp_path, bench.source_digest(), layout="aa"))
+    assert bench.profiled_traffic("droplet_128", "f32", "64x4", 32) is None
+    assert bench.profiled_traffic("droplet_128", "f32", "64x4", 32, layout="aa") == 601070592.0
+
+
+def _args(bench, argv):
+    import sys
+    old = sys.argv
+    sys.argv = ["bench.py"] + argv
+    try:
+        return bench.parse()
+    finally:
+        sys.argv = old
+
+
+def test_default_line_is_the_512_droplet_in_place(bench):
+    a = _args(bench, [])
+    assert a.workload == "droplet_512" and a.layout == "aa" and a.storage == "f32"
+    c = bench.arm_config(a, 1)
+    assert c["sites"] == 512 ** 3 and c["layout"] == "aa"
+    assert c["l2"].startswith("inputs larger than L2")
+
+
+def test_l2_note_is_true_for_small_lattices(bench):
+    a = _args(bench, ["--workload", "film_4x4x128"])
+    assert a.layout == "two"
+    assert bench.arm_config(a, 1)["l2"].startswith("populations fit in L2")
+
+
+@pytest.mark.parametrize("argv", [[], ["--workload", "droplet_128"], ["--workload", "ensemble_64"],
+                                  ["--workload", "serve"], ["--workload", "film_4x4x128", "--storage", "f16"]])
+def test_both_arms_print_the_same_config(bench, argv):
+    """The oracle arm's config is computed by the same function from the same
+    arguments: nothing in it depends on which arm runs."""
+    a = _args(bench, argv)
+    b = _args(bench, argv + ["--impl", "reference"])
+    assert bench.arm_config(a, 1) == bench.arm_config(b, 1)
