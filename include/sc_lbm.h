@@ -67,6 +67,13 @@ extern "C" {
 #define SC_STAGING_THREAD 1     /* each thread copies its site's 38 pulls (any nx) */
 #define SC_STAGING_ROWS 2       /* the CTA copies the tile's source rows as 16-byte chunks
                                    (nx a multiple of 4 for FP32, of 8 for FP16/BF16) */
+#define SC_STAGING_PERSISTENT 3 /* in place only (SC_LAYOUT_AA): one cooperative launch advances
+                                   many steps, each CTA keeping one tile column and ordering its
+                                   in-place writes against its neighbours' reads with bounded
+                                   progress waits (see SC_LAYOUT_AA). SC_STAGING_AUTO picks it
+                                   for in-place lattices when the device can keep one CTA per
+                                   tile column resident; SC_STAGING_THREAD keeps the two-pass
+                                   step. */
 
 /* Population storage between steps (streaming, Sec. II A: each population moves to
    the neighbour x + e_i, or back to x in the opposite direction where x + e_i is
@@ -81,11 +88,16 @@ extern "C" {
                                    writes each post-collision population f*_j into the slot
                                    that population opp(j) was read from. Since the force of
                                    Eq. (3) needs Psi of the neighbours before any of them is
-                                   overwritten, each step is two launches: Psi of every site
-                                   into an FP32 (Psi^r, Psi^b) array (8 bytes per site), then
-                                   stream + sink + force + collision in place. Results are
-                                   bit-identical to SC_LAYOUT_TWO_LATTICE. Not for batch
-                                   members. */
+                                   overwritten, the step is either one persistent cooperative
+                                   launch for many steps (SC_STAGING_PERSISTENT: each CTA owns a
+                                   tile column, forms Psi of the next plane of its tile and halo,
+                                   and waits, with a time limit, until its 8 neighbours have done
+                                   the same before it overwrites a plane; 304 bytes of DRAM per
+                                   FP32 site update) or two launches per step (SC_STAGING_THREAD:
+                                   Psi of every site into an FP32 (Psi^r, Psi^b) array, 8 bytes
+                                   per site, then stream + sink + force + collision in place;
+                                   472 bytes). Results are bit-identical to
+                                   SC_LAYOUT_TWO_LATTICE. Not for batch members. */
 
 /* Physical and geometric parameters of one lattice (Sec. II; geometry of Sec. III). */
 typedef struct sc_params {
@@ -133,7 +145,8 @@ typedef struct sc_diag {
                                      liquid base, linearly interpolated; -1 if none */
   double radius;                  /* (3 V / 4 pi)^(1/3), V = number of sites with rho^r > rho^b */
   int64_t droplet_sites;          /* V */
-  int32_t status;                 /* SC_OK, SC_ENONFINITE or SC_ESINKNEG */
+  int32_t status;                 /* SC_OK, SC_ENONFINITE, SC_ESINKNEG, or SC_ETIMEOUT after a
+                                     persistent in-place launch gave up a wait */
   int32_t reserved;
 } sc_diag;
 
@@ -240,6 +253,14 @@ int sc_lbm_launch_count(sc_lbm* h, int64_t nsteps, int64_t* launches);
 /* Name of the kernel (or kernels) that carries the step in the current configuration,
    a static string ("" for a NULL handle). */
 const char* sc_lbm_kernel_name(sc_lbm* h);
+/* Time limit of each progress wait of the persistent in-place step (default 2 s), and a
+   test hook: CTA withhold_cta (-1: none) never reports its progress, so its neighbours'
+   waits run out after limit_ns. A wait that runs out ends the launch early; the state
+   is then undefined, sc_lbm_sync returns SC_ETIMEOUT and diagnostics report status
+   SC_ETIMEOUT until a state is loaded (sc_lbm_init, _init_fields, _write_populations).
+   Nothing waits without a limit, so the device stays usable. No counterpart in the
+   paper. */
+int sc_lbm_set_wait(sc_lbm* h, int64_t limit_ns, int32_t withhold_cta);
 /* Bytes one sc_lbm_diagnostics / sc_lbm_profile call copies device-to-host. */
 int sc_lbm_diag_bytes(sc_lbm* h, size_t* bytes);
 /* Number of compiled tile shapes and their extents. */

@@ -16,6 +16,7 @@ from ._native import Diag, Init, Params, ScError, build, check
 
 Q = 19
 STORAGE = {"f32": 0, "f16": 1, "bf16": 2, "f16s": 3}
+STAGING = {"auto": 0, "thread": 1, "rows": 2, "persistent": 3}
 GEOMETRY = {"periodic": 0, "planar": 1, "sphere": 2}
 LAYOUT = {"two": 0, "aa": 1}
 
@@ -41,6 +42,8 @@ def make_params(params: dict) -> Params:
         p["geometry"] = GEOMETRY[p["geometry"]]
     if isinstance(p.get("layout"), str):
         p["layout"] = LAYOUT[p["layout"]]
+    if isinstance(p.get("staging"), str):
+        p["staging"] = STAGING[p["staging"]]
     return Params(**{k: p[k] for k, _ in Params._fields_})
 
 
@@ -243,7 +246,12 @@ class Lattice:
         tx, ty, zc, n, st = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int64(), C.c_int32()
         check(_lib().sc_lbm_launch_info(self._h, C.byref(tx), C.byref(ty), C.byref(zc), C.byref(n), C.byref(st)))
         return dict(tile_x=tx.value, tile_y=ty.value, zchunk=zc.value, ctas=n.value,
-                    staging={1: "thread", 2: "rows"}.get(st.value, st.value))
+                    staging={1: "thread", 2: "rows", 3: "persistent"}.get(st.value, st.value))
+
+    def set_wait(self, limit_ns: int, withhold_cta: int = -1) -> None:
+        """Time limit of the persistent in-place step's progress waits; withhold_cta >= 0
+        makes that CTA withhold its progress reports (a test of the failure path)."""
+        check(_lib().sc_lbm_set_wait(self._h, int(limit_ns), int(withhold_cta)))
 
 
 class Batch:

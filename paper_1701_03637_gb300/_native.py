@@ -113,6 +113,7 @@ _SIGS = {
     "sc_lbm_tune": (C.c_int, [_VP, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "sc_lbm_launch_count": (C.c_int, [_VP, C.c_int64, C.POINTER(C.c_int64)]),
     "sc_lbm_kernel_name": (C.c_char_p, [_VP]),
+    "sc_lbm_set_wait": (C.c_int, [_VP, C.c_int64, C.c_int32]),
     "sc_batch_create": (C.c_int, [C.c_size_t, C.c_int32, _VP, C.POINTER(_VP)]),
     "sc_batch_destroy": (None, [_VP]),
     "sc_batch_add": (C.c_int, [_VP, C.POINTER(Params), C.POINTER(C.c_int32), C.POINTER(_VP)]),

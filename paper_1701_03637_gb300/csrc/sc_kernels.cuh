@@ -92,9 +92,12 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
+// ldcg: a population read at L2 only (ld.global.cg), never from L1, for kernels in
+// which other CTAs of the same launch overwrite the data between two reads.
 struct StF32 {
   using T = float;
   static __device__ __forceinline__ float ld(const T* p, float) { return __ldg(p); }
+  static __device__ __forceinline__ float ldcg(const T* p, float) { return __ldcg(p); }
   static __device__ __forceinline__ float cv(T v, float) { return v; }
   static __device__ __forceinline__ void st(T* p, float v, float) { *p = v; }
   static __device__ __forceinline__ uint32_t pull_async(uint32_t* sm, const T* p) {
@@ -112,9 +115,13 @@ __device__ __forceinline__ uint32_t pull_async16(uint32_t* sm, const Half* p) {
   cp_async4(sm, reinterpret_cast<const void*>(a & ~uintptr_t(3)));
   return (uint32_t)(a >> 1) & 1u;
 }
+__device__ __forceinline__ unsigned short ldcg16(const void* p) {
+  return __ldcg(reinterpret_cast<const unsigned short*>(p));
+}
 struct StF16 {
   using T = __half;
   static __device__ __forceinline__ float ld(const T* p, float w) { return w + __half2float(__ldg(p)); }
+  static __device__ __forceinline__ float ldcg(const T* p, float w) { return w + __half2float(__ushort_as_half(ldcg16(p))); }
   static __device__ __forceinline__ float cv(T v, float w) { return w + __half2float(v); }
   static __device__ __forceinline__ void st(T* p, float v, float w) { *p = __float2half_rn(v - w); }
   static __device__ __forceinline__ uint32_t pull_async(uint32_t* sm, const T* p) { return pull_async16(sm, p); }
@@ -127,6 +134,9 @@ struct StF16 {
 struct StF16S {
   using T = __half;
   static __device__ __forceinline__ float ld(const T* p, float w) { return __fmul_rn(w, __half2float(__ldg(p))); }
+  static __device__ __forceinline__ float ldcg(const T* p, float w) {
+    return __fmul_rn(w, __half2float(__ushort_as_half(ldcg16(p))));
+  }
   static __device__ __forceinline__ float cv(T v, float w) { return __fmul_rn(w, __half2float(v)); }
   // w is a compile-time weight at every call, so 1 / w folds to a constant
   static __device__ __forceinline__ void st(T* p, float v, float w) { *p = __float2half_rn(__fmul_rn(v, 1.0f / w)); }
@@ -138,6 +148,9 @@ struct StF16S {
 struct StBF16 {
   using T = __nv_bfloat16;
   static __device__ __forceinline__ float ld(const T* p, float w) { return w + __bfloat162float(__ldg(p)); }
+  static __device__ __forceinline__ float ldcg(const T* p, float w) {
+    return w + __bfloat162float(__ushort_as_bfloat16(ldcg16(p)));
+  }
   static __device__ __forceinline__ float cv(T v, float w) { return w + __bfloat162float(v); }
   static __device__ __forceinline__ void st(T* p, float v, float w) { *p = __float2bfloat16_rn(v - w); }
   static __device__ __forceinline__ uint32_t pull_async(uint32_t* sm, const T* p) { return pull_async16(sm, p); }
@@ -914,6 +927,22 @@ __device__ __forceinline__ void aa_load(const LatDev& L, const typename S::T* A,
     const typename S::T* p = A + (long long)d * L.np + idx;
     fr[I] = S::cv(p[0], wgt(I));
     fb[I] = S::cv(p[cstride], wgt(I));
+  });
+}
+
+// The same loads at L2 only (the persistent in-place step, where neighbouring CTAs
+// rewrite slots this CTA read in an earlier step).
+template <class S, bool ODD>
+__device__ __forceinline__ void aa_load_cg(const LatDev& L, const typename S::T* A, const PullIdx& P, float (&fr)[Q],
+                                           float (&fb)[Q]) {
+  const long long cstride = (long long)Q * L.np;
+  Unroll<0, Q>::run([&](auto ic) {
+    constexpr int I = decltype(ic)::value;
+    int idx, d;
+    aa_slot<I, ODD>(P, idx, d);
+    const typename S::T* p = A + (long long)d * L.np + idx;
+    fr[I] = S::ldcg(p, wgt(I));
+    fb[I] = S::ldcg(p + cstride, wgt(I));
   });
 }
 

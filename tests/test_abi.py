@@ -52,7 +52,8 @@ def test_direction_table_matches_oracle_order(native, oracle_mod):
 @pytest.mark.parametrize("bad", [dict(nx=0), dict(tau_r=0.5), dict(geometry=7), dict(storage=5),
                                  dict(geometry=1, sink_layers=0), dict(wall_thickness=3, wall_z0=7),
                                  dict(geometry=2, R_H=0.0), dict(tile=99), dict(G=float("nan")),
-                                 dict(staging=3), dict(staging=2, nx=6), dict(zchunk=-1),
+                                 dict(staging=3), dict(staging=4), dict(staging=4, layout=1), dict(staging=2, nx=6),
+                                 dict(zchunk=-1),
                                  dict(staging=2, nx=12, storage="f16"), dict(layout=2), dict(layout=-1),
                                  dict(G_rr=float("inf")), dict(G_bb=float("nan"))])
 def test_invalid_params_rejected(native, bad):

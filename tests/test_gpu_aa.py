@@ -1,10 +1,12 @@
 """The in-place (AA) layout: the time step of Sec. II on one population lattice
-updated in place, two launches per step (Psi of every site, then stream + sink +
-force + collision). The state it reaches after any number of steps -- in either
-of its two storage forms -- is the two-lattice step's, bit for bit, for every
-storage type, geometry (walls, planar and spherical sinks) and ragged extent;
-it also matches the FP64 oracle directly, and checkpoints taken in either form
-restore into either layout."""
+updated in place, by either of its two kernels: the persistent cooperative step
+(one launch for many steps, CTAs ordered by bounded neighbour waits) or the
+two-pass step (Psi of every site, then stream + sink + force + collision). The
+state either reaches after any number of steps -- in either of its two storage
+forms -- is the two-lattice step's, bit for bit, for every storage type, geometry
+(walls, planar and spherical sinks) and ragged extent; it also matches the FP64
+oracle directly, and checkpoints taken in either form restore into either
+layout."""
 import numpy as np
 import pytest
 
@@ -51,8 +53,13 @@ def _cases():
 CASES = _cases()
 
 
-def _run(sc, params, init, steps, layout):
-    lat = sc.Lattice(dict(params, layout=layout))
+STAGINGS = ["persistent", "thread"]
+
+
+def _run(sc, params, init, steps, layout, staging="auto"):
+    lat = sc.Lattice(dict(params, layout=layout, staging=staging if layout == "aa" else "auto"))
+    if layout == "aa" and staging == "persistent":
+        assert lat.launch_info()["staging"] == "persistent"
     lat.init(init)
     out = []
     done = 0
@@ -73,13 +80,14 @@ def _same_diag(d, ref):
         assert d[k] == ref[k], (k, d[k], ref[k])
 
 
+@pytest.mark.parametrize("staging", STAGINGS)
 @pytest.mark.parametrize("storage", ["f32", "f16", "bf16", "f16s"])
 @pytest.mark.parametrize("case", list(CASES))
-def test_same_bits_as_two_lattices(sc, case, storage):
+def test_same_bits_as_two_lattices(sc, case, storage, staging):
     params, init = CASES[case]
     params = dict(params, storage=storage)
     steps = [1, 2, 7, 77, 150]  # odd and even forms; 64-step graphs replayed from both parities
-    aa = _run(sc, params, init, steps, "aa")
+    aa = _run(sc, params, init, steps, "aa", staging)
     two = _run(sc, params, init, steps, "two")
     for n, (fa, (ra, ba), da), (ft, (rt, bt), dt) in zip(steps, aa, two):
         assert np.array_equal(fa, ft), (case, storage, n)
@@ -87,9 +95,10 @@ def test_same_bits_as_two_lattices(sc, case, storage):
         _same_diag(da, dt)
 
 
+@pytest.mark.parametrize("staging", STAGINGS)
 @pytest.mark.parametrize("steps", [1, 2])
 @pytest.mark.parametrize("case", ["sphere_sink_ragged", "thin_column_mid_wall"])
-def test_random_state_matches_oracle(sc, oracle_mod, case, steps):
+def test_random_state_matches_oracle(sc, oracle_mod, case, steps, staging):
     """One and two in-place steps (the two forms) of a non-equilibrium state against
     the oracle, within 1e-6 of each population's scale as in the two-lattice tests."""
     from paper_1701_03637_gb300.workloads import random_populations
@@ -97,7 +106,7 @@ def test_random_state_matches_oracle(sc, oracle_mod, case, steps):
     nx, ny, nz = params["nx"], params["ny"], params["nz"]
     _, w = sc.lattice_directions()
     f0 = random_populations(nx, ny, nz, seed=4242 + nx, rho=(0.55, 0.25))
-    g = sc.Lattice(dict(params, layout="aa"))
+    g = sc.Lattice(dict(params, layout="aa", staging=staging))
     o = oracle_mod.Lattice(params)
     g.write_populations(f0)
     o.set_populations(f0)
@@ -114,10 +123,11 @@ def test_random_state_matches_oracle(sc, oracle_mod, case, steps):
     g.close()
 
 
+@pytest.mark.parametrize("staging", STAGINGS)
 @pytest.mark.parametrize("case", ["sphere_sink_ragged", "film_wall_sink"])
-def test_checkpoint_from_either_form_restores_into_either_layout(sc, case):
+def test_checkpoint_from_either_form_restores_into_either_layout(sc, case, staging):
     params, init = CASES[case]
-    src = sc.Lattice(dict(params, layout="aa"))
+    src = sc.Lattice(dict(params, layout="aa", staging=staging))
     src.init(init)
     for taken_at in (3, 8):  # odd form, then even form
         src.step(taken_at - src.diagnostics()["step"])
@@ -125,7 +135,7 @@ def test_checkpoint_from_either_form_restores_into_either_layout(sc, case):
         d = src.diagnostics()
         results = []
         for layout in ("aa", "two"):
-            dst = sc.Lattice(dict(params, layout=layout))
+            dst = sc.Lattice(dict(params, layout=layout, staging=staging if layout == "aa" else "auto"))
             dst.write_populations(f)
             dst.set_counters(d["step"], d["evaporated_mass"])
             dst.step(5)
@@ -154,14 +164,28 @@ def test_init_returns_to_the_even_form(sc):
 
 def test_launch_info_and_tuner_report_the_in_place_step(sc):
     params, init = CASES["periodic_two_segments"]
-    lat = sc.Lattice(dict(params, layout="aa"))
+    lat = sc.Lattice(dict(params, layout="aa", staging="thread"))
     lat.init(init)
     info = lat.launch_info()
     assert info["tile_y"] == 1 and info["zchunk"] == 1 and info["staging"] == "thread"
     assert info["tile_x"] == 128 and 1 <= info["ctas"] <= 2 * 17 * 21  # row segments of the lattice
+    assert lat.launch_count(10) == 20
     before = lat.read_populations()
     assert lat.tune() == dict(tile=0, zchunk=1)
     assert np.array_equal(lat.read_populations(), before)
+    lat.close()
+    # the automatic choice in place: the two-pass step on small planes, the persistent
+    # step (one CTA per tile column, the whole z extent) on planes of 2^17 sites or more
+    lat = sc.Lattice(dict(params, layout="aa"))
+    assert lat.launch_info()["staging"] == "thread"
+    lat.close()
+    big = dict(params, nx=512, ny=256, nz=4)
+    lat = sc.Lattice(dict(big, layout="aa"))
+    info = lat.launch_info()
+    assert info["staging"] == "persistent" and info["zchunk"] == big["nz"]
+    cols = -(-big["nx"] // info["tile_x"]) * -(-big["ny"] // info["tile_y"])
+    assert info["ctas"] == cols
+    assert lat.launch_count(10) == 1 and lat.launch_count(2049) == 3
     lat.close()
 
 
@@ -175,23 +199,36 @@ def test_batch_rejects_in_place_members(sc):
 
 @pytest.mark.parametrize("n", [128, 256])
 def test_full_size_droplet_same_bits(sc, n):
-    """The benchmark's droplet (planar sinks across the z seam) at 128^3 and 256^3:
-    densities equal to the two-lattice step's after an odd and an even number of
-    steps, compared on the device."""
+    """The benchmark's droplet (planar sinks across the z seam) at 128^3 and 256^3,
+    in place with either kernel: densities equal to the two-lattice step's after an
+    odd and an even number of steps, compared on the device."""
     import torch
     from paper_1701_03637_gb300.workloads import droplet
     params, init = droplet(n, 24.0 * n / 128, 1)
     fields = {}
-    for layout in ("aa", "two"):
-        lat = sc.Lattice(dict(params, layout=layout))
+    for kind in ("aa", "aa_thread", "two"):
+        layout = "two" if kind == "two" else "aa"
+        staging = {"aa": "persistent", "aa_thread": "thread", "two": "auto"}[kind]
+        lat = sc.Lattice(dict(params, layout=layout, staging=staging))
         lat.init(init)
         lat.step(9)
         f9 = lat.read_fields_device().clone()
         lat.step(11)
         f20 = lat.read_fields_device().clone()
-        fields[layout] = (f9, f20, lat.diagnostics())
+        fields[kind] = (f9, f20, lat.diagnostics())
         lat.close()
         torch.cuda.synchronize()
-    for k in (0, 1):
-        assert torch.equal(fields["aa"][k], fields["two"][k]), k
-    _same_diag(fields["aa"][2], fields["two"][2])
+    for kind in ("aa", "aa_thread"):
+        for k in (0, 1):
+            assert torch.equal(fields[kind][k], fields["two"][k]), (kind, k)
+        _same_diag(fields[kind][2], fields["two"][2])
+
+
+def test_more_steps_than_one_persistent_launch(sc):
+    """1031 steps are two persistent launches (1024 + 7), the second starting in the
+    odd form: the same bits as the two-lattice step."""
+    params, init = CASES["film_wall_sink"]
+    aa = _run(sc, params, init, [1031], "aa", "persistent")
+    two = _run(sc, params, init, [1031], "two")
+    assert np.array_equal(aa[0][0], two[0][0])
+    _same_diag(aa[0][2], two[0][2])
