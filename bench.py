@@ -13,7 +13,7 @@ The same lattice is also timed with FP16 and BF16 offset storage
 Metric: MLUPS (million site updates per second, both components per update).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload droplet_512|droplet_128|droplet_1024|film_4x4x128|ensemble_64|serve]
+                    [--workload droplet_512|droplet_128|droplet_256|droplet_1024|film_4x4x128|ensemble_64|serve]
                     [--layout two|aa] [--storage f32|f16|bf16|f16s]
 
 Under torchrun each rank advances its own copy of the lattice (independent
@@ -44,7 +44,7 @@ PROFILE_DIR = os.path.join(ROOT, "profiles")
 L2_BYTES = 129e6  # GB300 L2
 # population layout of each workload unless --layout says otherwise: the droplets
 # of 512^3 and more are the in-place (AA) configuration
-DEFAULT_LAYOUT = {"droplet_512": "aa", "droplet_1024": "aa"}
+DEFAULT_LAYOUT = {"droplet_256": "aa", "droplet_512": "aa", "droplet_1024": "aa"}
 # the oracle's sample of a workload too large for it: the 128^3 droplet of the same
 # recipe (radius / box = 0.1875), the crop-equivalent case of the precision study
 ORACLE_CROP_EDGE = 128
@@ -137,11 +137,13 @@ def profile_fields():
 
 
 def profiled_traffic(workload_name, storage, tile=None, zchunk=None, layout="two"):
-    """DRAM bytes per launch of the dominant kernel from a committed ncu summary, if
-    one was taken on the current kernel source, this workload, storage, layout and
-    launch configuration; None otherwise."""
+    """DRAM bytes per time step of the dominant kernel from a committed ncu summary
+    (dram_bytes_per_step, or dram_bytes_per_launch of a kernel that runs one step per
+    launch), if one was taken on the current kernel source, this workload, storage,
+    layout and launch configuration; None otherwise."""
     for kv in profile_fields():
-        if "dram_bytes_per_launch" not in kv:
+        key = "dram_bytes_per_step" if "dram_bytes_per_step" in kv else "dram_bytes_per_launch"
+        if key not in kv:
             continue
         if kv.get("source_digest") != source_digest() or kv.get("workload") != workload_name:
             continue
@@ -150,7 +152,7 @@ def profiled_traffic(workload_name, storage, tile=None, zchunk=None, layout="two
         if tile is not None and (kv.get("tile") != tile or kv.get("zchunk") != str(zchunk)):
             continue
         try:
-            return float(kv["dram_bytes_per_launch"])
+            return float(kv[key])
         except ValueError:
             continue
     return None
@@ -522,6 +524,7 @@ def run_ours(args):
             "traffic": profiled_traffic(args.workload, args.storage, tile_s, info["zchunk"], args.layout),
             "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
             "algorithmic_bytes_per_site": BYTES_PER_SITE[args.storage],
+            "traffic_per": "time step (DRAM bytes of one step, as achieved is per step)",
             "kernel": lat.kernel_name(), "launches_per_step": launches / args.steps}
 
     # end to end through the public API: initial densities from pinned host memory,

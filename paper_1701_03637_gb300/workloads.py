@@ -40,6 +40,7 @@ def droplet(n, radius, seed, rho_hi=1.0, rho_lo=0.03, rho_H=0.03, noise=1e-4, st
 WORKLOADS = {
     "film_4x4x128": lambda **kw: film_4x4x128(**kw),
     "droplet_128": lambda **kw: droplet(128, 24.0, 1, **kw),
+    "droplet_256": lambda **kw: droplet(256, 48.0, 2, **kw),
     "droplet_512": lambda **kw: droplet(512, 96.0, 2, **kw),
     # the same recipe at 1024^3 (R/N = 0.1875): in FP32 it fits one GPU only in place
     "droplet_1024": lambda **kw: droplet(1024, 192.0, 2, **kw),
