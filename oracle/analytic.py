@@ -209,3 +209,87 @@ def bulk_pressure(rho_r, rho_b, G, G_rr=0.0, G_bb=0.0):
     pr = psi(rr)
     pb = psi(rb)
     return cs2 * (rr + rb) + G * cs2 * pr * pb + 0.5 * cs2 * (G_rr * pr * pr + G_bb * pb * pb)
+
+
+# ---------------------------------------------------------------- diffusion column (Sec. III A)
+
+def _fick2_operator(rc, rb, left_c, left_b, g, tau, closed_left):
+    """Banded form of the spatial operator of Eq. (fick2) on sites 1..M (interleaved
+    unknowns [c_1, b_1, c_2, b_2, ...]): d rho^a_i / dt = flux_in - flux_out with the
+    face flux of Eq. (fick) F^a_{i+1/2} = -sum_b D^{ab}_{i+1/2} (rho^b_{i+1} - rho^b_i),
+    D^{ab} of Eq. (diffu-t-1) at the mean of the two sites' densities. Site 0 holds the
+    Dirichlet values (left_c, left_b) unless closed_left; the face past site M is closed
+    (the halfway wall). Returns (ab, rhs0): ab the (7, 2M) band of the operator for
+    scipy.linalg.solve_banded((3, 3), ...), rhs0 the Dirichlet contribution."""
+    M = len(rc)
+    c = np.concatenate([[left_c], rc])
+    b = np.concatenate([[left_b], rb])
+    cm, bm = 0.5 * (c[1:] + c[:-1]), 0.5 * (b[1:] + b[:-1])   # faces 1/2 .. M - 1/2
+    dcc, dcb = diffusion_matrix(cm, bm, g, tau)     # equation of c: D^{cc}, D^{c cbar}
+    dbb, dbc = diffusion_matrix(bm, cm, g, tau)     # equation of cbar: D^{cbar cbar}, D^{cbar c}
+    if closed_left:
+        dcc, dcb, dbb, dbc = (np.where(np.arange(M) == 0, 0.0, v) for v in (dcc, dcb, dbb, dbc))
+    # coefficient of face k (between site k and k + 1, k = 0..M-1) per (equation, variable);
+    # unknown 2 i + e is equation e at site i + 1, between faces i and i + 1 (the last closed)
+    K = {(0, 0): dcc, (0, 1): dcb, (1, 1): dbb, (1, 0): dbc}
+    n = 2 * M
+    ab = np.zeros((7, n))
+    rhs0 = np.zeros(n)
+    for (e, v), Dk in K.items():
+        Du = np.concatenate([Dk[1:], [0.0]])              # face above each site
+        ab[3 + e - v, v::2] -= Dk + Du                    # the site's own variable
+        ab[5 + e - v, v:n - 2:2] += Dk[1:]                # variable of the site below (rows 2..)
+        ab[1 + e - v, v + 2::2] += Dk[1:]                 # variable of the site above
+        rhs0[e] += Dk[0] * (left_c if v == 0 else left_b)  # the Dirichlet site 0
+    return ab, rhs0
+
+
+def fick2_column(M, times, rho_H, rho_cbar, g, tau=1.0, dt=2.0, rho_c0=None, rho_b0=None, closed_left=False,
+                 tol=1e-15, max_iter=50):
+    """Eq. (fick2) on the lattice sites of the diffusion column of Sec. III A: site 0 is
+    the evaporation boundary (rho^c = rho_H, rho^cbar = rho_cbar - rho_H, the sink's
+    complement of a total rho_cbar), sites 1..M hold the fluid (initially rho^c = 0,
+    rho^cbar = rho_cbar unless rho_c0 / rho_b0 are given), and the face past site M is
+    closed (halfway bounce-back at the wall). Eq. (fick2) is read as the divergence of
+    the fluxes of Eq. (fick), d rho^a/dt = div(sum_b D^{ab} grad rho^b), with the
+    coefficients of Eq. (diffu-t-1) at the local densities and the sign that makes it
+    dissipative; this is the printed form where D is constant, and it conserves mass.
+    Finite volumes of unit width, Crank-Nicolson in time with the coefficients at the
+    mid-step state, Picard-iterated until the step changes by less than tol. With
+    closed_left the face at site 0 is closed as well (site 0 then takes no part).
+    Returns {t: (rho_c[1..M], rho_cbar[1..M])} for t in times (multiples of dt)."""
+    from scipy.linalg import solve_banded
+    rc = np.zeros(M) if rho_c0 is None else np.array(rho_c0, np.float64)
+    rb = np.full(M, float(rho_cbar)) if rho_b0 is None else np.array(rho_b0, np.float64)
+    lc, lb = float(rho_H), float(rho_cbar) - float(rho_H)
+    out = {}
+    t = 0.0
+    want = sorted(times)
+    for T in want:
+        nsteps = int(round((T - t) / dt))
+        for _ in range(nsteps):
+            x0 = np.empty(2 * M)
+            x0[0::2], x0[1::2] = rc, rb
+            x = x0.copy()
+            for _ in range(max_iter):
+                mid = 0.5 * (x0 + x)
+                ab, rhs0 = _fick2_operator(mid[0::2], mid[1::2], lc, lb, g, tau, closed_left)
+                # (I - dt/2 L) x1 = (I + dt/2 L) x0 + dt * rhs0
+                Lx0 = rhs0 * 0.0
+                for d in range(-3, 4):
+                    row = ab[3 - d]
+                    if d >= 0:
+                        Lx0[: 2 * M - d] += row[d:] * x0[d:]
+                    else:
+                        Lx0[-d:] += row[: 2 * M + d] * x0[: 2 * M + d]
+                A = -0.5 * dt * ab
+                A[3] += 1.0
+                x1 = solve_banded((3, 3), A, x0 + 0.5 * dt * Lx0 + dt * rhs0)
+                done = np.max(np.abs(x1 - x)) <= tol
+                x = x1
+                if done:
+                    break
+            rc, rb = x[0::2].copy(), x[1::2].copy()
+        t += nsteps * dt
+        out[T] = (rc.copy(), rb.copy())
+    return out

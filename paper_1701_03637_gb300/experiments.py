@@ -174,10 +174,11 @@ def evaporating_film(nz=128, film_z=32, nxy=4, rho=(0.70, 0.04), rho_H=0.02, G=3
                 rho_ma=rho_ma, rho_mi=rho_mi, rho_b_vap=rho_b_vap, rho_H=rho_H, G=G)
 
 
-def fick_column(nz=128, nxy=4, rho_cbar=0.7, rho_H=0.001, G=3.6, tau=1.0, times=(3000, 10000), storage="f32"):
-    """The diffusion experiment of Sec. III A: a column of the other component
-    (rho^b = rho_cbar, rho^r = 0) between the evaporation boundary z = 0, which
-    holds rho^r = rho_H, and a wall of thickness 2 at the far end. Returns, at each
+def fick_column(nz=125, nxy=4, rho_cbar=0.7, rho_H=0.001, G=3.6, tau=1.0, times=(3000, 10000), storage="f32"):
+    """The diffusion experiment of Sec. III A (the paper's 125 x 4 x 4 sites by
+    default): a column of the other component (rho^b = rho_cbar, rho^r = 0) between
+    the evaporation boundary z = 0, which holds rho^r = rho_H, and a wall of thickness
+    2 at the far end (the last two planes). Returns, at each
     time, the xy-mean profiles of rho^r and rho^b and the z flux of r relative to
     the mixture, rho^r (U^r - U) of Eqs. (flux) and (velw) (tau = 1), evaluated on
     the device (sc_lbm_flux_profile)."""
