@@ -60,9 +60,13 @@ def parse():
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16", "f16s"])
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--zchunk", type=int, default=0)
-    ap.add_argument("--layout", default=None, choices=["two", "aa"],
-                    help="two population lattices, or one updated in place (half the memory); "
-                         "default: in place for the 512^3 and 1024^3 droplets, two lattices otherwise")
+    ap.add_argument("--layout", default=None, choices=["two", "aa", "slab"],
+                    help="two population lattices, or one updated in place (half the memory), or one "
+                         "lattice split along z over the ranks (two lattices per slab, ghost planes "
+                         "exchanged every step); default: in place for the 256^3 - 1024^3 droplets, "
+                         "two lattices otherwise")
+    ap.add_argument("--staging", default="auto", choices=["auto", "thread", "rows", "persistent"],
+                    help="how the step kernel gathers its populations (in place: persistent or the two-pass step)")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip timing the other storage types on the default workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -76,10 +80,10 @@ def parse():
     return args
 
 
-def workload(name, storage, tile=0, zchunk=0, layout="two"):
+def workload(name, storage, tile=0, zchunk=0, layout="two", staging="auto"):
     from paper_1701_03637_gb300.workloads import WORKLOADS
     params, init = WORKLOADS[name](storage=storage)
-    params.update(tile=tile, zchunk=zchunk, layout=layout)
+    params.update(tile=tile, zchunk=zchunk, layout=layout, staging=staging)
     return params, init
 
 
@@ -202,7 +206,9 @@ def workload_config(args, params, world):
             "sites": params["nx"] * params["ny"] * params["nz"], "lattices_per_gpu": 1,
             "storage": args.storage, "layout": args.layout,
             "l2": l2_note(population_bytes(params, args.storage, args.layout)),
-            "parallelism": f"independent replicas x{world}"}
+            "parallelism": (f"one lattice split along z over {world} ranks, 2 ghost planes per side exchanged "
+                            f"every step ({2 * 19 * 2 * params['nx'] * params['ny'] * (4 if args.storage == 'f32' else 2)}"
+                            f" bytes per face)") if args.layout == "slab" else f"independent replicas x{world}"}
 
 
 def launch_cfg(lat):
@@ -482,7 +488,7 @@ def run_ours(args):
     def slowest(v):
         return max_over_ranks(v, world, "cuda")
 
-    params, init = workload(args.workload, args.storage, args.tile, args.zchunk, args.layout)
+    params, init = workload(args.workload, args.storage, args.tile, args.zchunk, args.layout, args.staging)
     n = params["nx"] * params["ny"] * params["nz"]
     aa = args.layout == "aa"
     need, free = sc.required_bytes(params), torch.cuda.mem_get_info()[0]
@@ -493,8 +499,8 @@ def run_ours(args):
     lat = sc.Lattice(params)
     lat.init(init)
     tuned = None
-    if not args.tile and not args.zchunk and not args.no_tune:
-        tuned = lat.tune(trials=20)  # untimed; leaves the state unchanged
+    if not args.tile and not args.zchunk and not args.no_tune and not aa:
+        tuned = lat.tune(trials=20)  # untimed; leaves the state unchanged (in place: nothing to tune)
     stream = torch.cuda.current_stream()
     lat.step(args.warmup)
     torch.cuda.synchronize()
@@ -570,7 +576,7 @@ def run_ours(args):
         lat.close()
         variants = {}
         for st in ("f16", "bf16"):
-            vp, vi = workload(args.workload, st, 0, 0, args.layout)
+            vp, vi = workload(args.workload, st, 0, 0, args.layout, args.staging)
             v = sc.Lattice(vp)
             v.init(vi)
             v.tune(trials=5)
@@ -887,10 +893,93 @@ def run_serve(args):
         dist.destroy_process_group()
 
 
+def run_slab(args):
+    """One lattice of the workload split along z over the ranks (one slab per GPU,
+    slab_ranges), every step exchanging the slabs' 2 boundary planes with the
+    neighbouring ranks (NCCL; a single rank is its own neighbour) before the fused
+    step: strong scaling, value = the whole lattice's site updates / the slowest
+    rank's time."""
+    import torch
+    import torch.distributed as dist
+
+    import paper_1701_03637_gb300 as sc
+    from paper_1701_03637_gb300.slab import DistributedSlab, LocalSlabs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    sc.build()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    params, init = workload(args.workload, args.storage, args.tile, args.zchunk, "two")
+    n = params["nx"] * params["ny"] * params["nz"]
+    if world > 1:
+        part = DistributedSlab(params)
+        slab, stepper = part.slab, part
+    else:
+        part = LocalSlabs(params, 1)
+        slab, stepper = part.slabs[0], part
+    slab.init(init)
+    stream = torch.cuda.current_stream()
+    stepper.step(args.warmup)
+    torch.cuda.synchronize()
+    sampler = ClockSampler()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.time()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    stepper.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    t1 = time.time()
+    sampler.stop()
+    ms = e0.elapsed_time(e1)
+    ms_max = max_over_ranks(ms, world, "cuda")
+    stepper.sync()
+    d = slab.diagnostics()
+    bad = sum_over_ranks(1.0 if d["status"] != 0 else 0.0, world, "cuda")
+    own = params["nx"] * params["ny"] * (slab.z1 - slab.z0)
+    value = n * args.steps / (ms_max * 1e-3) / 1e6
+    peak, peak_kind = measured_peak_hbm()
+    achieved = BYTES_PER_SITE[args.storage] * own / (ms * 1e-3 / args.steps) / 1e9
+    if rank == 0:
+        info = slab.launch_info()
+        cfg = workload_config(args, params, world)
+        out = {"metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+               "scaling": "strong", "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
+               "config": cfg,
+               "launch": {"tile": f"{info['tile_x']}x{info['tile_y']}", "zchunk": info["zchunk"],
+                          "ctas": info["ctas"], "staging": info["staging"], "slab_planes": slab.z1 - slab.z0},
+               "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                            "frac": achieved / peak, "traffic": None,
+                            "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                            "algorithmic_bytes_per_site": BYTES_PER_SITE[args.storage],
+                            "note": "rank 0's step including its ghost exchange"},
+               "cpu_baseline": None, "e2e": None, "gpu_launches": slab.launch_count(args.steps),
+               "clocks": sampler.summary(t0, t1), "ranks_with_bad_status": bad}
+        print(json.dumps(out))
+    part.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.layout == "slab":
+        run_slab(args)
     elif args.workload == "ensemble_64":
         run_ensemble(args)
     elif args.workload == "serve":

@@ -229,7 +229,8 @@ int sc_lbm_flux_profile(sc_lbm* h, double* j_host);
    The first call on a device (and the first after the device's context has been
    destroyed and recreated, e.g. by cudaDeviceReset) looks up the array's device
    address, so it should come before any stream capture on that device. All calls
-   on a device share the array: calls whose work overlaps on the GPU race. */
+   on a device share the array: calls whose work overlaps on the GPU race. Slabs
+   (sc_slab_create) are rejected with SC_EINVAL. */
 int sc_lbm_diagnostics_noalloc(sc_lbm* h, double* out_dev);
 
 /* Kernel configuration in use: tile extents, planes per CTA, grid size and the
@@ -265,6 +266,37 @@ int sc_lbm_set_wait(sc_lbm* h, int64_t limit_ns, int32_t withhold_cta);
 int sc_lbm_diag_bytes(sc_lbm* h, size_t* bytes);
 /* Number of compiled tile shapes and their extents. */
 int sc_tile_list(int32_t* count, int32_t* tx_host, int32_t* ty_host, int32_t capacity);
+
+/* ---------------------------------------------------------------- z slabs of one lattice
+   One lattice split along z over several handles (one per GPU or rank). The step of
+   Sec. II is local except for streaming and the force of Eq. (3), which reach one plane
+   across a slab's faces (periodic boundaries with forces computed across them, Sec.
+   II A). A slab holds planes [z0, z1) of the lattice described by the global
+   parameters, plus 2 ghost planes on each side: before every step each slab sends its
+   2 lowest and 2 highest planes (every population, as the current buffer holds them) to
+   the ghost planes of its lower and upper neighbour (periodic in z), then steps as an
+   ordinary two-lattice handle. Its geometry (sinks, walls, sphere) and its seeded
+   initial state are the whole lattice's, so its own planes evolve exactly as the same
+   planes of one lattice would, bit for bit. The paper has no counterpart: this
+   distributes the one step it describes. Two-lattice layout only. */
+
+/* A slab of planes [z0, z1) (z1 - z0 >= 2) of the lattice described by `global`; its
+   handle's nz is z1 - z0 + 4 (local plane 2 is plane z0). Every sc_lbm_* call applies
+   to it; populations and fields are its local planes, ghosts included. Its diagnostics
+   count its own planes only (mass_r, mass_b, evaporated_mass, flux_last,
+   droplet_sites); interface_z and radius need the whole lattice's sums. */
+int sc_slab_create(const sc_params* global, int32_t z0, int32_t z1, void* stream, sc_lbm** out);
+/* Planes [z0, z1), ghost planes per side, and the bytes of one face's exchange
+   (2 * 19 populations of 2 planes). Any output may be NULL. */
+int sc_slab_info(sc_lbm* h, int32_t* z0, int32_t* z1, int32_t* ghosts, size_t* face_bytes);
+/* Copy the slab's 2 lowest (side 0) or 2 highest (side 1) own planes of the current
+   buffer into out_dev (face_bytes of caller-owned device memory: population array k's
+   2 planes at offset k * face_bytes / 38), asynchronously on the handle's stream. */
+int sc_slab_pack(sc_lbm* h, int32_t side, void* out_dev);
+/* Copy a neighbour's packed planes into the ghost planes below (side 0) or above
+   (side 1) the slab's own planes: side 0 takes the lower neighbour's side-1 pack,
+   side 1 the upper neighbour's side-0 pack. Asynchronous on the handle's stream. */
+int sc_slab_unpack(sc_lbm* h, int32_t side, const void* in_dev);
 
 /* Thread-local message describing the last failure (never NULL). */
 const char* sc_last_error(void);

@@ -72,7 +72,20 @@ struct LatDev {
   int geometry, sink_z0, sink_layers;  // sink_z0 in [0, nz)
   double scx, scy, scz, RH2;
   int wall_z0, wall_z1;    // solid slab [wall_z0, wall_z1)
+  // z-slab of a larger lattice: local plane z is plane (z + zoff) mod nzg of the lattice
+  // whose geometry (sinks, walls, sphere) these fields describe; planes [own0, own1) are
+  // the slab's own, the rest ghosts whose evaporation is not booked. A whole lattice has
+  // zoff = 0, nzg = nz, own0 = 0, own1 = nz.
+  int zoff, nzg, own0, own1;
 };
+
+// Plane of the whole lattice that local plane z is (z in [0, nz)).
+__device__ __forceinline__ int global_z(const LatDev& L, int z) {
+  int g = z + L.zoff;
+  g = g >= L.nzg ? g - L.nzg : g;
+  return g >= L.nzg ? g - L.nzg : g;
+}
+__device__ __forceinline__ bool own_z(const LatDev& L, int z) { return z >= L.own0 && z < L.own1; }
 
 // ------------------------------------------------------------------ storage types
 // ld: a population from global memory. pull_async: start a 4-byte asynchronous
@@ -169,16 +182,20 @@ __host__ __device__ __forceinline__ int wrap_near(int v, int n) {
   return (unsigned)v < (unsigned)n ? v : wrapi(v, n);
 }
 
-__device__ __forceinline__ bool solid_z(const LatDev& L, int z) { return z >= L.wall_z0 && z < L.wall_z1; }
+__device__ __forceinline__ bool solid_z(const LatDev& L, int z) {
+  const int g = global_z(L, z);
+  return g >= L.wall_z0 && g < L.wall_z1;
+}
 
 // Site class from coordinates (no storage): solid slab, planar or spherical sink.
 // The squared distance is formed without FMA contraction so it rounds like a
-// plain host evaluation.
-__device__ __forceinline__ int site_class(const LatDev& L, int x, int y, int z) {
-  if (solid_z(L, z)) return SOLID;
+// plain host evaluation. z is a local plane; the geometry is the whole lattice's.
+__device__ __forceinline__ int site_class(const LatDev& L, int x, int y, int zl) {
+  if (solid_z(L, zl)) return SOLID;
+  const int z = global_z(L, zl);
   if (L.geometry == 1) {
-    const int dz = z - L.sink_z0;  // sink_z0 in [0, nz), z in [0, nz)
-    return (dz < 0 ? dz + L.nz : dz) < L.sink_layers ? SINK : FLUID;
+    const int dz = z - L.sink_z0;  // sink_z0 in [0, nzg), z in [0, nzg)
+    return (dz < 0 ? dz + L.nzg : dz) < L.sink_layers ? SINK : FLUID;
   }
   if (L.geometry == 2) {
     const double dx = (double)x - L.scx, dy = (double)y - L.scy, dz = (double)z - L.scz;
@@ -564,7 +581,7 @@ struct Tile {
       rr = sum19(fr);
       rb = sum19(fb);
       if (cls == SINK) {
-        if (active && own) evap += (double)sink_excess(L, fr);
+        if (active && own && own_z(L, wrapz(p))) evap += (double)sink_excess(L, fr);
         sink_densities(L, rr, rb);
       }
       pr = psi_of(rr);
@@ -798,7 +815,7 @@ struct TileRows {
       rr = sum19(fr);
       rb = sum19(fb);
       if (cls == SINK) {
-        if (active && own) evap += (double)sink_excess(L, fr);
+        if (active && own && own_z(L, zp)) evap += (double)sink_excess(L, fr);
         sink_densities(L, rr, rb);
       }
       pr = psi_of(rr);

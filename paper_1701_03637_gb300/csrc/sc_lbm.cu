@@ -462,7 +462,7 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag(const LatDev L, const typ
   // non-finite flag, negative-complement flag
   constexpr int NF = 7;
   double acc[NF] = {0, 0, 0, 0, 0, 0, 0};
-  if (!solid_z(L, z)) {
+  if (!solid_z(L, z) && own_z(L, z)) {  // a slab's ghost planes are not its own
     for (int q = b + threadIdx.x; q < e; q += blockDim.x) {
       const int x = q % L.nx, y = q / L.nx;
       const int cls = site_class(L, x, y, z);
@@ -691,15 +691,17 @@ __global__ void k_load(const LatDev L, typename S::T* __restrict__ dst, long lon
       for (int i = 0; i < Q; ++i) { fr[i] = wgt(i) * r; fb[i] = wgt(i) * b; }
     } else {
       bool rich;
+      const int zg = global_z(L, z);  // the shape and the noise are the whole lattice's
+      const long long sg = (long long)x + (long long)L.nx * ((long long)y + (long long)L.ny * zg);
       if (sh.shape == 0) {
-        rich = z < sh.film_z;
+        rich = zg < sh.film_z;
       } else {
-        const double dx = (double)x - sh.cx, dy = (double)y - sh.cy, dz = (double)z - sh.cz;
+        const double dx = (double)x - sh.cx, dy = (double)y - sh.cy, dz = (double)zg - sh.cz;
         rich = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)) < sh.R2;
       }
-      const double ur = (double)(splitmix64_at(sh.seed, 1ULL + (unsigned long long)s) >> 11) * 0x1.0p-53;
+      const double ur = (double)(splitmix64_at(sh.seed, 1ULL + (unsigned long long)sg) >> 11) * 0x1.0p-53;
       const double ub =
-          (double)(splitmix64_at(sh.seed, 1ULL + (unsigned long long)nsites + (unsigned long long)s) >> 11) * 0x1.0p-53;
+          (double)(splitmix64_at(sh.seed, 1ULL + (unsigned long long)nsites + (unsigned long long)sg) >> 11) * 0x1.0p-53;
       const double r = (rich ? sh.hi : sh.lo) + __dmul_rn(sh.amp, __dadd_rn(2.0 * ur, -1.0));
       const double b = (rich ? sh.lo : sh.hi) + __dmul_rn(sh.amp, __dadd_rn(2.0 * ub, -1.0));
 #pragma unroll
@@ -799,6 +801,7 @@ StepOps step_ops(int storage, int tile, bool rows) {
 }
 
 constexpr long long kMaxCtas = 4096;  // evaporated-mass slots, one per CTA of the persistent step
+constexpr int kSlabGhosts = 2;        // ghost planes on each side of a z-slab
 
 size_t elem_size(int storage) { return storage == SC_STORAGE_F32 ? 4 : 2; }
 
@@ -913,6 +916,10 @@ LatDev make_dev(const sc_params* p, const Layout& l) {
   L.scx = p->sphere_cx; L.scy = p->sphere_cy; L.scz = p->sphere_cz; L.RH2 = p->R_H * p->R_H;
   if (p->wall_thickness > 0) { L.wall_z0 = p->wall_z0; L.wall_z1 = p->wall_z0 + p->wall_thickness; }
   else { L.wall_z0 = 0; L.wall_z1 = 0; }
+  L.zoff = 0;
+  L.nzg = p->nz;
+  L.own0 = 0;
+  L.own1 = p->nz;
   return L;
 }
 
@@ -941,6 +948,7 @@ struct sc_lbm {
   long long wait_limit_ns;   // limit of each of its waits
   int withhold;              // CTA that withholds its progress reports (-1: none)
   const char* persist_why;   // why the persistent step was not planned
+  bool slab;                 // z-slab of a larger lattice (sc_slab_create)
   int zmax;  // planes of the longest work item
   cudaGraphExec_t graph;
   int graph_len;
@@ -1283,7 +1291,7 @@ int launch_load(sc_lbm* h, long long s0, long long s1, int mode, const float* f,
                 long long rs, const ShapeDev& sh) {
   // the pull reads the current buffer, so the load writes it
   k_load<S><<<grid_for(s1 - s0, 256), 256, 0, h->stream>>>(h->L, (typename S::T*)h->pop(h->cur), s0, s1, mode, f, fs,
-                                                            rho, rs, sh, h->lay.nsites);
+                                                            rho, rs, sh, (long long)h->p.nx * h->p.ny * h->L.nzg);
   CK(cudaGetLastError());
   return SC_OK;
 }
@@ -1309,6 +1317,12 @@ int launch_diag(sc_lbm* h) {
                                                   h->diag(), h->odd());
   CK(cudaGetLastError());
   return SC_OK;
+}
+
+// Whether local plane z lies in the solid slab (the whole lattice's plane numbers).
+bool host_solid(const sc_lbm* h, int z) {
+  int g = (z + h->L.zoff) % h->L.nzg;
+  return h->L.wall_z0 <= g && g < h->L.wall_z1;
 }
 
 int reset_counters(sc_lbm* h) {
@@ -1728,7 +1742,7 @@ int sc_lbm_profile(sc_lbm* h, double* phi) {
   const int ns = h->lay.diag_nsplit;
   const double nxy = (double)h->p.nx * h->p.ny;
   for (int z = 0; z < h->p.nz; ++z) {
-    if (h->L.wall_z0 <= z && z < h->L.wall_z1) { phi[z] = NAN; continue; }
+    if (host_solid(h, z)) { phi[z] = NAN; continue; }
     double acc = 0.0;
     for (int k = 0; k < ns; ++k) acc += h->h_diag[((size_t)z * ns + k) * kDiagFields + 2];
     phi[z] = acc / nxy;
@@ -1758,7 +1772,7 @@ int sc_lbm_diagnostics(sc_lbm* h, sc_diag* d) {
       nonfinite = std::max(nonfinite, q[5]);
       sinkneg = std::max(sinkneg, q[6]);
     }
-    phi[z] = (h->L.wall_z0 <= z && z < h->L.wall_z1) ? NAN : pz / nxy;
+    phi[z] = host_solid(h, z) ? NAN : pz / nxy;
   }
   double cum = 0.0;
   for (long long k = 0; k < h->lay.nslots; ++k) cum += h->h_evap[k];
@@ -1785,6 +1799,7 @@ int sc_lbm_diagnostics(sc_lbm* h, sc_diag* d) {
 int sc_lbm_diagnostics_noalloc(sc_lbm* h, double* out_dev) {
   Range range("sc_lbm_diagnostics_noalloc");
   if (!h || !out_dev) return fail(SC_EINVAL, "NULL argument");
+  if (h->slab) return fail(SC_EINVAL, "diagnostics without allocation take whole lattices, not slabs");
   const long long need = (long long)h->p.nz * h->lay.diag_nsplit * kDiagFields;
   if (need > kNoAllocScratch)
     return fail(SC_EINVAL, "diagnostics without allocation need %lld doubles of scratch, the limit is %lld (nz too large)",
@@ -1876,6 +1891,86 @@ int sc_lbm_tune(sc_lbm* h, int32_t trials, int32_t* tile, int32_t* zchunk) {
   if (tile) *tile = h->lay.tile + 1;
   if (zchunk) *zchunk = h->zmax;
   return SC_OK;
+}
+
+// ------------------------------------------------------------------ z slabs of one lattice
+
+int sc_slab_create(const sc_params* g, int32_t z0, int32_t z1, void* stream, sc_lbm** out) {
+  int rc = validate(g);
+  if (rc) return rc;
+  if (!out) return fail(SC_EINVAL, "out is NULL");
+  if (g->layout != SC_LAYOUT_TWO_LATTICE) return fail(SC_EINVAL, "slabs use the two-lattice layout");
+  if (z0 < 0 || z1 > g->nz || z1 - z0 < kSlabGhosts)
+    return fail(SC_EINVAL, "slab planes [%d, %d) must lie in [0, %d) and number at least %d", z0, z1, g->nz,
+                kSlabGhosts);
+  const int nloc = z1 - z0 + 2 * kSlabGhosts;
+  if ((long long)g->nx * g->ny * nloc > (1LL << 31) - 4096) return fail(SC_EINVAL, "slab too large");
+  // the handle's own parameters describe the local planes; the geometry stays the whole
+  // lattice's (set in its LatDev below)
+  sc_params lp = *g;
+  lp.nz = nloc;
+  lp.wall_thickness = 0;
+  lp.wall_z0 = 0;
+  lp.sink_z0 = 0;
+  lp.sink_layers = std::min(g->sink_layers, nloc);
+  if (lp.geometry == SC_GEOM_PLANAR_SINK && lp.sink_layers < 1) lp.sink_layers = 1;
+  const Layout l = make_layout(&lp);
+  void* buf = nullptr;
+  cudaError_t e = cudaMalloc(&buf, l.total);
+  if (e != cudaSuccess) return fail(SC_ENOMEM, "cudaMalloc(%zu) failed: %s", l.total, cudaGetErrorString(e));
+  sc_lbm* h = nullptr;
+  rc = create_common(&lp, stream, buf, true, &h);
+  if (rc) return rc;
+  const LatDev G = make_dev(g, l);
+  h->L.wall_z0 = G.wall_z0;
+  h->L.wall_z1 = G.wall_z1;
+  h->L.sink_z0 = G.sink_z0;
+  h->L.sink_layers = G.sink_layers;
+  h->L.nzg = g->nz;
+  h->L.zoff = ((z0 - kSlabGhosts) % g->nz + g->nz) % g->nz;
+  h->L.own0 = kSlabGhosts;
+  h->L.own1 = kSlabGhosts + (z1 - z0);
+  h->slab = true;
+  *out = h;
+  return SC_OK;
+}
+
+int sc_slab_info(sc_lbm* h, int32_t* z0, int32_t* z1, int32_t* ghosts, size_t* face_bytes) {
+  if (!h) return fail(SC_EINVAL, "NULL handle");
+  if (!h->slab) return fail(SC_EINVAL, "not a slab");
+  if (z0) *z0 = (h->L.zoff + kSlabGhosts) % h->L.nzg;
+  if (z1) *z1 = (h->L.zoff + kSlabGhosts) % h->L.nzg + (h->L.own1 - h->L.own0);
+  if (ghosts) *ghosts = kSlabGhosts;
+  if (face_bytes) *face_bytes = (size_t)2 * Q * kSlabGhosts * h->p.nx * h->p.ny * elem_size(h->p.storage);
+  return SC_OK;
+}
+
+// The kSlabGhosts planes starting at local plane zl of the current buffer, as 2 * 19
+// arrays of kSlabGhosts * nx * ny elements each, to or from a packed device buffer.
+static int slab_copy(sc_lbm* h, int zl, void* packed, bool to_packed) {
+  const size_t es = elem_size(h->p.storage);
+  const size_t run = (size_t)kSlabGhosts * h->p.nx * h->p.ny * es;  // contiguous in each array
+  char* planes = (char*)h->pop(h->cur) + (size_t)zl * h->p.nx * h->p.ny * es;
+  const size_t pitch = (size_t)h->lay.np * es;
+  if (to_packed)
+    CK(cudaMemcpy2DAsync(packed, run, planes, pitch, run, 2 * Q, cudaMemcpyDeviceToDevice, h->stream));
+  else
+    CK(cudaMemcpy2DAsync(planes, pitch, packed, run, run, 2 * Q, cudaMemcpyDeviceToDevice, h->stream));
+  return SC_OK;
+}
+
+int sc_slab_pack(sc_lbm* h, int32_t side, void* out_dev) {
+  if (!h || !out_dev) return fail(SC_EINVAL, "NULL argument");
+  if (!h->slab) return fail(SC_EINVAL, "not a slab");
+  if (side != 0 && side != 1) return fail(SC_EINVAL, "side must be 0 (low) or 1 (high)");
+  return slab_copy(h, side == 0 ? h->L.own0 : h->L.own1 - kSlabGhosts, out_dev, true);
+}
+
+int sc_slab_unpack(sc_lbm* h, int32_t side, const void* in_dev) {
+  if (!h || !in_dev) return fail(SC_EINVAL, "NULL argument");
+  if (!h->slab) return fail(SC_EINVAL, "not a slab");
+  if (side != 0 && side != 1) return fail(SC_EINVAL, "side must be 0 (low) or 1 (high)");
+  return slab_copy(h, side == 0 ? 0 : h->L.own1, (void*)in_dev, false);
 }
 
 int sc_lbm_launch_count(sc_lbm* h, int64_t nsteps, int64_t* launches) {

@@ -92,3 +92,11 @@ def test_both_arms_print_the_same_config(bench, argv):
     a = _args(bench, argv)
     b = _args(bench, argv + ["--impl", "reference"])
     assert bench.arm_config(a, 1) == bench.arm_config(b, 1)
+
+
+def test_slab_layout_config(bench):
+    a = _args(bench, ["--workload", "droplet_128", "--layout", "slab"])
+    b = _args(bench, ["--workload", "droplet_128", "--layout", "slab", "--impl", "reference"])
+    c = bench.arm_config(a, 4)
+    assert c == bench.arm_config(b, 4) and c["layout"] == "slab"
+    assert "split along z over 4 ranks" in c["parallelism"] and str(2 * 19 * 2 * 128 * 128 * 4) in c["parallelism"]
