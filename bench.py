@@ -74,6 +74,8 @@ def parse():
     ap.add_argument("--no-tune", action="store_true", help="keep the automatic kernel configuration")
     ap.add_argument("--requests", type=int, default=40, help="serve workload: requests in the stream")
     ap.add_argument("--rate", type=float, default=20.0, help="serve workload: arrivals per second")
+    ap.add_argument("--light-rate", type=float, default=4.0,
+                    help="serve workload: arrivals per second of the sub-capacity stream (a quarter as many requests)")
     args = ap.parse_args()
     if args.layout is None:
         args.layout = DEFAULT_LAYOUT.get(args.workload, "two")
@@ -815,17 +817,17 @@ def run_serve(args):
             dist.barrier()
         return gather_results(run(mine), world)
 
-    def batched_server(cap=0):
+    def batched_server(cap=0, st=None):
         def run(mine):
-            srv = Server(arena, storage, max_active_sites=cap)
+            srv = Server(arena, st or storage, max_active_sites=cap)
             out = srv.run(mine)
             srv.close()
             return out
         return run
 
-    def stream(count, rate, seed):
+    def stream(count, rate, seed, st=None):
         return [Request(k, t, p, i, n) for k, (t, p, i, n) in
-                enumerate(request_stream(count, rate, seed, storage=storage))]
+                enumerate(request_stream(count, rate, seed, storage=st or storage))]
 
     def summary(res, wall):
         lat = [r.latency for r in res]
@@ -850,22 +852,35 @@ def run_serve(args):
     res_all = served(over, batched_server())
     uncapped = summary(res_all, max(r.finished for r in res_all))
 
-    light = stream(max(4, args.requests // 4), args.rate / 20.0, 5)
+    light = stream(max(4, args.requests // 4), args.light_rate, 5)
     res_light = served(light, batched_server(cap))
     light_s = summary(res_light, max(r.finished for r in res_light))
 
+    # the same stream with FP16 of the scaled populations f / w (same relative spacing
+    # in liquid and vapour), for its error against FP32
+    scaled = stream(args.requests, args.rate, 4, "f16s")
+    res_scaled = served(scaled, batched_server(cap, "f16s"))
+    scaled_s = summary(res_scaled, max(r.finished for r in res_scaled))
+
     seq = served(over, lambda mine: serve_one_at_a_time(mine, "f32"))
     seq_s = summary(seq, max(r.finished for r in seq))
-    # error of the served FP16 runs against the same runs in FP32 (FP32 matches the
-    # FP64 oracle to 1e-4 in density after 1000 steps): the observable of each
-    # run's last record (interface position for films, radius for droplets)
-    errs = []
-    for a, b in zip(res, seq):
-        if a.status or b.status:
-            continue  # an evicted run has no final observable (counted in failed_runs)
-        k = 1 if over[a.rid].init["shape"] == 0 else 2
-        errs.append(abs(a.series[-1][k] - b.series[-1][k]))
-    failed = {"batched": sum(1 for r in res if r.status), "one_at_a_time_fp32": sum(1 for r in seq if r.status)}
+
+    def observable_errors(runs):
+        """|final observable - FP32's| per run (interface position for films, radius for
+        droplets, lattice units); FP32 matches the FP64 oracle to 1e-4 in density after
+        1000 steps. Evicted runs have no final observable (counted in failed_runs)."""
+        out = []
+        for a, b in zip(runs, seq):
+            if a.status or b.status:
+                continue
+            k = 1 if over[a.rid].init["shape"] == 0 else 2
+            out.append(abs(a.series[-1][k] - b.series[-1][k]))
+        return out
+
+    errs = observable_errors(res)
+    errs_scaled = observable_errors(res_scaled)
+    failed = {"batched": sum(1 for r in res if r.status), "one_at_a_time_fp32": sum(1 for r in seq if r.status),
+              "batched_scaled_f16": sum(1 for r in res_scaled if r.status)}
     clk = sampler.summary(t0, t1)
     work = sum(r.sites * r.steps for r in res)
     if rank != 0:
@@ -880,13 +895,17 @@ def run_serve(args):
            "launch": {"site_updates": work, "arena_bytes": arena},
            "serving": {"batched": uncapped,
                        "batched_site_cap": dict(batched, max_active_sites=cap),
-                       "sub_capacity": dict(light_s, rate_per_s=args.rate / 20.0),
+                       "sub_capacity": dict(light_s, rate_per_s=args.light_rate),
                        "one_at_a_time_fp32": seq_s,
                        "failed_runs": failed,
-                       "observable_abs_error_vs_fp32": {"max": max(errs, default=float("nan")),
-                                                        "median": percentile(errs, 50),
-                                                        "what": "final interface position (films) or radius "
-                                                                "(droplets), lattice units"}},
+                       "batched_scaled_f16": dict(scaled_s, max_active_sites=cap),
+                       "observable_abs_error_vs_fp32": {
+                           storage: {"max": max(errs, default=float("nan")), "median": percentile(errs, 50),
+                                     "p99": percentile(errs, 99)},
+                           "f16s": {"max": max(errs_scaled, default=float("nan")),
+                                    "median": percentile(errs_scaled, 50), "p99": percentile(errs_scaled, 99)},
+                           "what": "final interface position (films) or radius (droplets) of each served run "
+                                   "against the same run in FP32, lattice units"}},
            "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": clk}
     print(json.dumps(out))
     if world > 1:
