@@ -298,6 +298,42 @@ int sc_slab_pack(sc_lbm* h, int32_t side, void* out_dev);
    side 1 the upper neighbour's side-0 pack. Asynchronous on the handle's stream. */
 int sc_slab_unpack(sc_lbm* h, int32_t side, const void* in_dev);
 
+/* ---------------------------------------------------------------- more than two components
+   The paper names the extension of its two-component model to more components as
+   straightforward (Sec. I); Eq. (3) already sums the force over the other components
+   cbar. ncomp components (2 to SC_MAX_COMP) on a periodic lattice with an optional solid
+   slab (halfway bounce-back, Psi = 0 at solid sites); the paper states its evaporation
+   boundary for two components only, so there is no sink. Each component c has its
+   relaxation time tau[c]; g[c][cbar] is the coupling g^{c cbar} of Eq. (3) (the diagonal
+   the self couplings). The common velocity is u' = sum_c (m^c / tau_c) /
+   sum_c (rho^c / tau_c) and the shift tau_c F^c / rho^c, as for two components. FP32
+   populations, two lattices, two launches per step (Psi of every component and site,
+   then pull + force + collision). With two components and non-zero self couplings the
+   populations are bit-identical to sc_lbm_step's. */
+#define SC_MAX_COMP 4
+
+typedef struct sc_nparams {
+  int32_t nx, ny, nz;             /* lattice extent, each >= 1 */
+  int32_t ncomp;                  /* components, 2 .. SC_MAX_COMP */
+  double tau[SC_MAX_COMP];        /* relaxation times (> 0.5) of the first ncomp components */
+  double g[SC_MAX_COMP][SC_MAX_COMP];  /* couplings g^{c cbar}; finite */
+  int32_t wall_z0, wall_thickness;/* solid slab z in [wall_z0, wall_z0 + wall_thickness); 0 = none */
+} sc_nparams;
+
+typedef struct sc_ncomp sc_ncomp;
+
+/* Create (cudaMalloc of two population lattices and the Psi array) on `stream`. */
+int sc_ncomp_create(const sc_nparams* p, void* stream, sc_ncomp** out);
+void sc_ncomp_destroy(sc_ncomp* h);
+/* Canonical populations f[c][i][s] (ncomp * 19 * nx*ny*nz doubles, converted to FP32);
+   solid sites are ignored. Synchronous. */
+int sc_ncomp_write_populations(sc_ncomp* h, const double* f_host);
+/* Canonical populations out (same layout; 0 at solid sites). Synchronous. */
+int sc_ncomp_read_populations(sc_ncomp* h, double* f_host);
+/* Advance nsteps steps (asynchronous, two launches per step). */
+int sc_ncomp_step(sc_ncomp* h, int64_t nsteps);
+int sc_ncomp_sync(sc_ncomp* h);
+
 /* Thread-local message describing the last failure (never NULL). */
 const char* sc_last_error(void);
 

@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(PKG, "_build")
 LIB_PATH = os.path.join(BUILD_DIR, "libsc_lbm.so")
 SOURCES = ["sc_lbm.cu"]
-HEADERS = ["sc_kernels.cuh", "sc_batch.cuh"]
+HEADERS = ["sc_kernels.cuh", "sc_batch.cuh", "sc_ncomp.cuh"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 _lock = threading.Lock()
@@ -76,6 +76,15 @@ class Init(C.Structure):
                 ("seed", C.c_uint64)]
 
 
+MAX_COMP = 4
+
+
+class NParams(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("ncomp", C.c_int32),
+                ("tau", C.c_double * MAX_COMP), ("g", (C.c_double * MAX_COMP) * MAX_COMP),
+                ("wall_z0", C.c_int32), ("wall_thickness", C.c_int32)]
+
+
 class Diag(C.Structure):
     _fields_ = [("step", C.c_int64), ("mass_r", C.c_double), ("mass_b", C.c_double),
                 ("evaporated_mass", C.c_double), ("flux_last", C.c_double),
@@ -119,6 +128,12 @@ _SIGS = {
                                C.POINTER(C.c_size_t)]),
     "sc_slab_pack": (C.c_int, [_VP, C.c_int32, _VP]),
     "sc_slab_unpack": (C.c_int, [_VP, C.c_int32, _VP]),
+    "sc_ncomp_create": (C.c_int, [C.POINTER(NParams), _VP, C.POINTER(_VP)]),
+    "sc_ncomp_destroy": (None, [_VP]),
+    "sc_ncomp_write_populations": (C.c_int, [_VP, _VP]),
+    "sc_ncomp_read_populations": (C.c_int, [_VP, _VP]),
+    "sc_ncomp_step": (C.c_int, [_VP, C.c_int64]),
+    "sc_ncomp_sync": (C.c_int, [_VP]),
     "sc_batch_create": (C.c_int, [C.c_size_t, C.c_int32, _VP, C.POINTER(_VP)]),
     "sc_batch_destroy": (None, [_VP]),
     "sc_batch_add": (C.c_int, [_VP, C.POINTER(Params), C.POINTER(C.c_int32), C.POINTER(_VP)]),

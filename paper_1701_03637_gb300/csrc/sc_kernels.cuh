@@ -398,9 +398,8 @@ __device__ __forceinline__ float cdot(const float (&u)[3]) {
 // u_eq = u' + tau_c F^c / rho^c with F^c = -Psi^c(x) g A: g = G and A = a^cbar =
 // sum_i w_i Psi^cbar(x + e_i) e_i in the paper's two-component model, g = 1 and
 // A = sum_cbar g^{c cbar} a^cbar (coupled_sums) with self couplings.
-__device__ __forceinline__ void relax(const LatDev& L, int c, float (&f)[Q], float rho, float ps, float g,
-                                      const float (&A)[3], const float (&up)[3]) {
-  const float om = c == 0 ? L.omega[0] : L.omega[1], tau = c == 0 ? L.tau[0] : L.tau[1];
+__device__ __forceinline__ void relax_core(float om, float tau, float (&f)[Q], float rho, float ps, float g,
+                                           const float (&A)[3], const float (&up)[3]) {
   // tau F / rho = (-g tau) (Psi / rho) A with Psi / rho <= 1, so a trace (or
   // denormal) density cannot overflow the shift; rho = 0 takes u' itself
   const float q = rho > 0.0f ? __fdiv_rn(ps, rho) : 0.0f;
@@ -427,6 +426,10 @@ __device__ __forceinline__ void relax(const LatDev& L, int c, float (&f)[Q], flo
     f[I] = __fmaf_rn(om, __fsub_rn(__fadd_rn(ev, od), f[I]), f[I]);
     f[J] = __fmaf_rn(om, __fsub_rn(__fsub_rn(ev, od), f[J]), f[J]);
   });
+}
+__device__ __forceinline__ void relax(const LatDev& L, int c, float (&f)[Q], float rho, float ps, float g,
+                                      const float (&A)[3], const float (&up)[3]) {
+  relax_core(c == 0 ? L.omega[0] : L.omega[1], c == 0 ? L.tau[0] : L.tau[1], f, rho, ps, g, A, up);
 }
 
 // A^c = sum_cbar g^{c cbar} a^cbar of Eq. (3): the cross coupling g (= g^{rb} = g^{br})
@@ -479,6 +482,24 @@ __device__ __forceinline__ void force_sums(PsiAt2 psi2, int sm1, int s0, int sp1
     if (ex != 0) { acc(ar[0], ex, dr); acc(ab[0], ex, db); }
     if (ey != 0) { acc(ar[1], ey, dr); acc(ab[1], ey, db); }
     if (ez != 0) { acc(ar[2], ez, dr); acc(ab[2], ez, db); }
+  });
+}
+
+// sum_i w_i Psi(x + e_i) e_i of one component, with force_sums' order of operations;
+// psi1(plane slot, ly, lx) yields that component's Psi.
+template <class PsiAt1>
+__device__ __forceinline__ void force_sum_one(PsiAt1 psi1, int sm1, int s0, int sp1, int ly, int lx, float (&a)[3]) {
+  a[0] = a[1] = a[2] = 0.f;
+  Unroll<0, 9>::run([&](auto kc) {
+    constexpr int I = 1 + 2 * decltype(kc)::value;
+    constexpr int ex = dir_x(I), ey = dir_y(I), ez = dir_z(I);
+    const int sa = ez > 0 ? sp1 : (ez < 0 ? sm1 : s0);
+    const int sb = ez > 0 ? sm1 : (ez < 0 ? sp1 : s0);
+    const float d = __fsub_rn(psi1(sa, ly + ey, lx + ex), psi1(sb, ly - ey, lx - ex));
+    auto acc = [&](float& v, int e) { v = __fmaf_rn(e > 0 ? wgt(I) : -wgt(I), d, v); };
+    if (ex != 0) acc(a[0], ex);
+    if (ey != 0) acc(a[1], ey);
+    if (ez != 0) acc(a[2], ez);
   });
 }
 

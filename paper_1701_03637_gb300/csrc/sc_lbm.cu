@@ -2007,3 +2007,4 @@ int sc_lbm_diag_bytes(sc_lbm* h, size_t* bytes) {
 }  // extern "C"
 
 #include "sc_batch.cuh"
+#include "sc_ncomp.cuh"
