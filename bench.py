@@ -75,7 +75,7 @@ def parse():
     ap.add_argument("--requests", type=int, default=40, help="serve workload: requests in the stream")
     ap.add_argument("--rate", type=float, default=20.0, help="serve workload: arrivals per second")
     ap.add_argument("--light-rate", type=float, default=4.0,
-                    help="serve workload: arrivals per second of the sub-capacity stream (a quarter as many requests)")
+                    help="serve workload: arrivals per second of the lighter stream (a quarter as many requests)")
     args = ap.parse_args()
     if args.layout is None:
         args.layout = DEFAULT_LAYOUT.get(args.workload, "two")
@@ -855,6 +855,8 @@ def run_serve(args):
     light = stream(max(4, args.requests // 4), args.light_rate, 5)
     res_light = served(light, batched_server(cap))
     light_s = summary(res_light, max(r.finished for r in res_light))
+    light_work = sum(r.sites * r.steps for r in res_light)
+    work_all = sum(r.sites * r.steps for r in res_all)
 
     # the same stream with FP16 of the scaled populations f / w (same relative spacing
     # in liquid and vapour), for its error against FP32
@@ -895,7 +897,12 @@ def run_serve(args):
            "launch": {"site_updates": work, "arena_bytes": arena},
            "serving": {"batched": uncapped,
                        "batched_site_cap": dict(batched, max_active_sites=cap),
-                       "sub_capacity": dict(light_s, rate_per_s=args.light_rate),
+                       # offered site updates per second (rate x mean work of a request) against
+                       # what the batched server sustained: above 1 the queue still builds
+                       "light_stream": dict(light_s, rate_per_s=args.light_rate,
+                                            offered_vs_served=args.light_rate * light_work / len(light) / 1e6
+                                            / uncapped["mlups"]),
+                       "offered_vs_served": args.rate * work_all / len(over) / 1e6 / uncapped["mlups"],
                        "one_at_a_time_fp32": seq_s,
                        "failed_runs": failed,
                        "batched_scaled_f16": dict(scaled_s, max_active_sites=cap),
