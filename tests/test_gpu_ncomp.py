@@ -48,8 +48,9 @@ def test_matches_the_n_component_oracle(sc, n, wall, steps):
     gl.step(steps)
     o.step(steps)
     fg, fo = gl.read_populations(), o.f
+    # each population's own scale max(|f|, w_i rho^c), as in the two-component parity tests
     rho = np.abs(fo).sum(axis=1, keepdims=True)
-    den = np.maximum(np.maximum(np.abs(fo), multi.W[None, :, None, None, None] * rho * 1e-3), 1e-30)
+    den = np.maximum(np.maximum(np.abs(fo), multi.W[None, :, None, None, None] * rho), 1e-30)
     err = np.max(np.abs(fg - fo) / den)
     assert err < 1e-6 * steps, err
     gl.close()
