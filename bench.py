@@ -96,7 +96,7 @@ def describe(name, params, storage):
     shape = "film on a wall" if params.get("wall_thickness", 0) else "droplet"
     return (f"{name}: {params['nx']}x{params['ny']}x{params['nz']} two-component D3Q19 Shan-Chen {shape}, "
             f"{geom}, tau=1, G=3.6, rho_H={params['rho_H']}, {storage} populations, "
-            + ("one lattice in place (AA: Psi pass + collision)" if params.get("layout") == "aa"
+            + ("one lattice updated in place (AA pattern)" if params.get("layout") == "aa"
                else "two-lattice pull"))
 
 
