@@ -610,8 +610,9 @@ def run_ours(args):
                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
                "config": workload_config(args, params, world),
-               "launch": {"tile": tile_s, "zchunk": info["zchunk"], "ctas": info["ctas"],
-                          "staging": info["staging"], "autotuned": tuned is not None},
+               "launch": dict({"tile": tile_s, "zchunk": info["zchunk"], "ctas": info["ctas"],
+                               "staging": info["staging"], "autotuned": tuned is not None},
+                              **({"bands": info["bands"]} if "bands" in info else {})),
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                "clocks": clk, "diag": {k: d[k] for k in ("mass_r", "mass_b", "evaporated_mass", "radius")}}
         if variants is not None:

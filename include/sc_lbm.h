@@ -262,6 +262,21 @@ const char* sc_lbm_kernel_name(sc_lbm* h);
    Nothing waits without a limit, so the device stays usable. No counterpart in the
    paper. */
 int sc_lbm_set_wait(sc_lbm* h, int64_t limit_ns, int32_t withhold_cta);
+/* Bands of the persistent in-place step. That step marches the lattice in `bands`
+   bands of equal width along x, one after another within every step; each band is
+   the paper's time step (Sec. II) restricted to its sites, its halo at a band edge
+   being Psi saved by the band before it or the arrived populations of the band after
+   it, so the result is the same for any band count, bit for bit. More bands keep a
+   plane of a band in the L2 between its two reads, and make the step possible on
+   planes whose tiles would not fit its shared-memory ring with one band. request: -1
+   reports the current count only; 0 restores the automatic count (the fewest powers
+   of two, dividing nx, for which a tile grid fits); k >= 1 uses k bands (k must
+   divide nx into bands of at least 2 sites) and re-plans the tile grid for the
+   following steps. *bands (may be NULL) receives the count in use, 0 for a lattice
+   without the persistent step. SC_EINVAL for a request on such a lattice, for a k that
+   does not divide nx, or when no tile grid fits k bands (the previous plan is kept).
+   Tuning and test hook; no counterpart in the paper. */
+int sc_lbm_persist_bands(sc_lbm* h, int32_t request, int32_t* bands);
 /* Bytes one sc_lbm_diagnostics / sc_lbm_profile call copies device-to-host. */
 int sc_lbm_diag_bytes(sc_lbm* h, size_t* bytes);
 /* Number of compiled tile shapes and their extents. */

@@ -131,10 +131,13 @@ class Lattice:
 
     # ------------------------------------------------------------ lifecycle
     def close(self):
+        """Destroy the handle (after its stream has finished) and release its device
+        memory to torch's allocator."""
         h = getattr(self, "_h", None)
         if h is not None and h.value and getattr(self, "_owner", None) is None:
             _lib().sc_lbm_destroy(h)
         self._h = None
+        self._mem = None
 
     def __del__(self):
         try:
@@ -245,8 +248,18 @@ class Lattice:
     def launch_info(self) -> dict:
         tx, ty, zc, n, st = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int64(), C.c_int32()
         check(_lib().sc_lbm_launch_info(self._h, C.byref(tx), C.byref(ty), C.byref(zc), C.byref(n), C.byref(st)))
-        return dict(tile_x=tx.value, tile_y=ty.value, zchunk=zc.value, ctas=n.value,
-                    staging={1: "thread", 2: "rows", 3: "persistent"}.get(st.value, st.value))
+        out = dict(tile_x=tx.value, tile_y=ty.value, zchunk=zc.value, ctas=n.value,
+                   staging={1: "thread", 2: "rows", 3: "persistent"}.get(st.value, st.value))
+        if out["staging"] == "persistent":
+            out["bands"] = self.persist_bands()
+        return out
+
+    def persist_bands(self, request: int = -1) -> int:
+        """Bands along x of the persistent in-place step: -1 reports the count in use,
+        0 restores the automatic count, k >= 1 marches k bands (re-planning the tiles)."""
+        b = C.c_int32()
+        check(_lib().sc_lbm_persist_bands(self._h, int(request), C.byref(b)))
+        return int(b.value)
 
     def set_wait(self, limit_ns: int, withhold_cta: int = -1) -> None:
         """Time limit of the persistent in-place step's progress waits; withhold_cta >= 0

@@ -123,6 +123,7 @@ _SIGS = {
     "sc_lbm_launch_count": (C.c_int, [_VP, C.c_int64, C.POINTER(C.c_int64)]),
     "sc_lbm_kernel_name": (C.c_char_p, [_VP]),
     "sc_lbm_set_wait": (C.c_int, [_VP, C.c_int64, C.c_int32]),
+    "sc_lbm_persist_bands": (C.c_int, [_VP, C.c_int32, C.POINTER(C.c_int32)]),
     "sc_slab_create": (C.c_int, [C.POINTER(Params), C.c_int32, C.c_int32, _VP, C.POINTER(_VP)]),
     "sc_slab_info": (C.c_int, [_VP, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                C.POINTER(C.c_size_t)]),

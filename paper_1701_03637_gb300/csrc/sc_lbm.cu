@@ -182,37 +182,51 @@ __global__ void __launch_bounds__(kAAThreads, 4) k_aa_collide(const LatDev L, ty
 
 // ------------------------------------------------------------------ persistent in-place (AA) step
 //
-// One cooperative launch advances K steps. CTA b owns tile column b of a cx x cy
-// grid of TX x TY tiles for every step and marches its planes z = 0 .. nz-1: it
+// One cooperative launch advances K steps. The lattice is cut along x into B bands
+// of equal width, marched one after another in every step (B = 1: the whole
+// lattice at once). CTA k owns tile k of a cx x cy grid of TX x TY tiles over a
+// band, in every band and every step, and marches its planes z = 0 .. nz-1: it
 // forms Psi of plane p + 1 for its tile and a one-site halo ring (the halo from the
 // neighbours' arrived populations) into a shared ring, then streams, applies the
 // sink, forms the force and collides plane p and stores f* in place. Every
-// population is read from DRAM once (the collision reads it again at L2) and
-// written once: 304 bytes per FP32 site update, against 472 for the two-pass step.
+// population is read once by the Psi phase and once more by the collision, one
+// plane later; the bands keep that second read an L2 hit on large planes (a plane
+// of a 512^2 FP32 lattice is 40 MB, and three of them do not stay in the L2).
 //
 // What orders the CTAs: a site's arrived populations (its read set, which equals
 // its write set) are overwritten only when its owner collides it, and a neighbour
 // reads them (for its halo Psi) one plane earlier. So before colliding plane p a
 // CTA waits until its 8 neighbours have formed Psi of plane p ("psi_done"), and
-// before a step it waits until they have written the previous step ("steps_done").
-// Both are 64-bit counters per CTA, released after a barrier and polled with
-// acquire loads, tagged with the launch number in the high 32 bits. All CTAs are
-// resident (cooperative launch), so the waits always end; each is still bounded by
-// a time limit after which the CTA records where it gave up in `err` and returns
-// (every other CTA then gives up too), and the host reports SC_ETIMEOUT. The
-// planes nz - 1 (the halo below plane 0) and 0 (the halo above plane nz - 1) are
+// before a band it waits until they have finished the previous band ("steps_done",
+// one count per band). Both are 64-bit counters per CTA, released after a barrier
+// and polled with acquire loads, tagged with the launch number in the high 32 bits.
+// All CTAs are resident (cooperative launch), so the waits always end; each is still
+// bounded by a time limit after which the CTA records where it gave up in `err` and
+// returns (every other CTA then gives up too), and the host reports SC_ETIMEOUT.
+// The planes nz - 1 (the halo below plane 0) and 0 (the halo above plane nz - 1) are
 // formed first and kept in two extra ring slots, since both are rewritten before
 // the march needs them again. Population loads bypass L1 (ld.global.cg): a line a
 // CTA cached in one step may have been rewritten by a neighbour by the next.
-constexpr int kPersistMaxSteps = 1024;  // steps per launch: the counters of one launch stay below 2^32
+//
+// Band edges: when band b is marched, band b - 1 is finished (its populations
+// overwritten) and band b + 1 not yet started (its populations still this step's
+// arrived ones). So the halo column left of band b > 0 is Psi that band b - 1 saved
+// from its last column, the halo right of band B - 1 is Psi that band 0 saved from
+// its first column, and every other halo comes from the populations. The saved
+// columns ("edge", [k][nz][ny]) are rewritten one step later, after every reader
+// has finished the band that read them (the band count).
+constexpr int kPersistMaxSteps = 1024;  // steps per launch (fewer when K B (nz + 2) would reach 2^32)
 constexpr int kRingSlots = 6;           // rolling planes (4), plane nz - 1, plane 0 kept for the wrap
 
 struct AAPersist {
-  int cx, cy, TX, TY;           // tile grid and tile extents
+  int cx, cy, TX, TY;           // tile grid over a band, and tile extents
+  int B, bw;                    // bands along x, marched one after another, and their width
   int K, odd0;                  // steps of this launch; form of its first step
   unsigned long long epoch;     // launch number << 32
   unsigned long long* psi_done;    // [cx * cy]
-  unsigned long long* steps_done;  // [cx * cy]
+  unsigned long long* steps_done;  // [cx * cy]: bands finished
+  float2* edge;                 // saved Psi columns: [k][nz][ny], k = b for band b's last column
+                                // (b < B - 1), k = B - 1 for band 0's first column
   int* err;                     // 0, or 1 + where a wait gave up
   long long limit_ns;           // wait limit
   int withhold;                 // this CTA never reports its Psi planes (-1: none): makes its
@@ -256,42 +270,55 @@ template <class S, int NT>
 struct PersistTile {
   using T = typename S::T;
   const LatDev& L;
+  const AAPersist& a;
   T* A;
   float2* ring;
-  int x0, y0, tw, th, RW, cells;
+  int bx, by, band, x0, y0, tw, th, RW, cells;
 
   __device__ __forceinline__ int slot_of(int q) const {
     return (q == -1 || q == L.nz - 1) ? 4 : (q == L.nz ? 5 : (q & 3));
   }
   __device__ __forceinline__ float2& cell(int slot, int c) const { return ring[slot * cells + c]; }
-
-  // Ring cell c: its lattice site, or false past a ragged tile's halo.
-  __device__ __forceinline__ bool cell_site(int c, int& x, int& y) const {
-    const int hx = c % RW - 1, hy = c / RW - 1;
-    x = wrap_near(x0 + hx, L.nx);
-    y = wrap_near(y0 + hy, L.ny);
-    return hx <= tw && hy <= th;
+  __device__ __forceinline__ float2* edge_at(int k, int z, int y) const {
+    return a.edge + ((long long)k * L.nz + z) * L.ny + y;
   }
 
   // Psi of plane q (in [-1, nz]) over the tile and its halo ring into ring slot sa
   // (and sb >= 0); the 38 loads of a cell are independent and in flight together.
+  // Ring cell c is site (x0 + hx, y0 + hy), hx = c % RW - 1, hy = c / RW - 1
+  // (periodic); cells past a ragged tile's halo are skipped.
   template <bool ODD>
   __device__ __forceinline__ void psi_plane(int q, int sa, int sb) {
     const int zq = q < 0 ? q + L.nz : (q >= L.nz ? q - L.nz : q);
     const bool solid = solid_z(L, zq);
+    const bool left_saved = a.B > 1 && bx == 0 && band > 0;               // band band - 1's last column
+    const bool right_saved = a.B > 1 && bx == a.cx - 1 && band == a.B - 1;  // band 0's first column
+    const bool save_last = a.B > 1 && bx == a.cx - 1 && band < a.B - 1;
+    const bool save_first = a.B > 1 && bx == 0 && band == 0;
     for (int c = threadIdx.x; c < cells; c += NT) {
-      int x, y;
-      if (!cell_site(c, x, y)) continue;
+      const int hx = c % RW - 1, hy = c / RW - 1;
+      if (hx > tw || hy > th) continue;
+      const int x = wrap_near(x0 + hx, L.nx), y = wrap_near(y0 + hy, L.ny);
       float2 v = make_float2(0.f, 0.f);
       if (!solid) {
-        float fr[Q], fb[Q];
-        aa_load_cg<S, ODD>(L, A, PullIdx(L, x, y, zq), fr, fb);
-        float rr = sum19(fr), rb = sum19(fb);
-        if (site_class(L, x, y, zq) == SINK) sink_densities(L, rr, rb);
-        v = make_float2(psi_of(rr), psi_of(rb));
+        if (hx == -1 && left_saved) {
+          v = __ldcg(edge_at(band - 1, zq, y));
+        } else if (hx == tw && right_saved) {
+          v = __ldcg(edge_at(a.B - 1, zq, y));
+        } else {
+          float fr[Q], fb[Q];
+          aa_load_cg<S, ODD>(L, A, PullIdx(L, x, y, zq), fr, fb);
+          float rr = sum19(fr), rb = sum19(fb);
+          if (site_class(L, x, y, zq) == SINK) sink_densities(L, rr, rb);
+          v = make_float2(psi_of(rr), psi_of(rb));
+        }
       }
       cell(sa, c) = v;
       if (sb >= 0) cell(sb, c) = v;
+      if (hy >= 0 && hy < th) {
+        if (save_last && hx == tw - 1) *edge_at(band, zq, y) = v;
+        if (save_first && hx == 0) *edge_at(a.B - 1, zq, y) = v;
+      }
     }
   }
 
@@ -325,12 +352,12 @@ struct PersistTile {
     }
   }
 
-  // One step of the march, one barrier per plane: the neighbours' progress for the
-  // plane about to be written is polled before the Psi of the next plane is formed,
-  // and the barrier after it both completes the ring and publishes the poll; thread 0
-  // then reports the new Psi plane. False when a wait gave up.
+  // The march of one band in one step, one barrier per plane: the neighbours'
+  // progress for the plane about to be written is polled before the Psi of the next
+  // plane is formed, and the barrier after it both completes the ring and publishes
+  // the poll; thread 0 then reports the new Psi plane. False when a wait gave up.
   template <bool ODD>
-  __device__ __forceinline__ bool step(const AAPersist& a, int bx, int by, unsigned long long base, double& evap) {
+  __device__ __forceinline__ bool march(unsigned long long base, double& evap) {
     const int nz = L.nz;
     const bool reports = (int)blockIdx.x != a.withhold;
     psi_plane<ODD>(nz - 1, 4, -1);
@@ -355,27 +382,33 @@ struct PersistTile {
 // NT threads per CTA (128 or 256), 512 / NT CTAs per SM at 128 registers.
 template <class S, int NT>
 __global__ void __launch_bounds__(NT, 512 / NT)
-    k_aa_persist(const LatDev L, typename S::T* A, double* __restrict__ evap_cum, const AAPersist a) {
+    k_aa_persist(const LatDev L, typename S::T* A, double* __restrict__ evap_cum, const __grid_constant__ AAPersist a) {
   extern __shared__ __align__(16) float2 ring[];
   const int bx = (int)blockIdx.x % a.cx, by = (int)blockIdx.x / a.cx;
-  PersistTile<S, NT> t{L, A, ring, bx * a.TX, by * a.TY, 0, 0, a.TX + 2, (a.TX + 2) * (a.TY + 2)};
-  t.tw = min(a.TX, L.nx - t.x0);
+  PersistTile<S, NT> t{L, a, A, ring, bx, by, 0, 0, by * a.TY, 0, 0, a.TX + 2, (a.TX + 2) * (a.TY + 2)};
+  t.tw = min(a.TX, a.bw - bx * a.TX);
   t.th = min(a.TY, L.ny - t.y0);
   double evap = 0.0;
-  const unsigned long long per_step = (unsigned long long)L.nz + 2;
-  for (int s = 0; s < a.K; ++s) {
-    // the neighbours have written the previous step (their slots this step reads)
-    if (s > 0) {
-      bool ok = true;
-      if (threadIdx.x < 9) ok = poll_neighbour(a, a.steps_done, a.epoch + (unsigned long long)s, bx, by, 0);
-      if (__syncthreads_or(!ok)) break;
+  const unsigned long long per_band = (unsigned long long)L.nz + 2;
+  bool ok = true;
+  for (int s = 0; s < a.K && ok; ++s) {
+    for (int b = 0; b < a.B && ok; ++b) {
+      const unsigned long long sb = (unsigned long long)s * a.B + b;  // bands this launch marched before
+      // the neighbours have finished the previous band (this band's populations are
+      // their last writes; the saved edge columns are complete and read no more)
+      if (sb > 0) {
+        bool got = true;
+        if (threadIdx.x < 9) got = poll_neighbour(a, a.steps_done, a.epoch + sb, bx, by, 0);
+        if (__syncthreads_or(!got)) { ok = false; break; }
+      }
+      t.band = b;
+      t.x0 = b * a.bw + bx * a.TX;
+      const unsigned long long base = a.epoch + sb * per_band;
+      ok = ((a.odd0 + s) & 1) ? t.template march<true>(base, evap) : t.template march<false>(base, evap);
+      if (!ok) break;
+      __syncthreads();  // every store and saved column of the band, then the report
+      if (threadIdx.x == 0) st_release_u64(a.steps_done + blockIdx.x, a.epoch + sb + 1);
     }
-    const unsigned long long base = a.epoch + (unsigned long long)s * per_step;
-    const bool ok = ((a.odd0 + s) & 1) ? t.template step<true>(a, bx, by, base, evap)
-                                       : t.template step<false>(a, bx, by, base, evap);
-    if (!ok) break;
-    __syncthreads();  // every store of the step, then the report
-    if (threadIdx.x == 0) st_release_u64(a.steps_done + blockIdx.x, a.epoch + (unsigned long long)s + 1);
   }
   if (L.geometry != 0) {
     __shared__ double red[NT / 32];
@@ -941,7 +974,9 @@ struct sc_lbm {
   int grid_psi;  // CTAs of k_aa_psi
   // persistent in-place step (k_aa_persist), when the layout is in place and it fits
   bool persist;
-  int pcx, pcy, ptx, pty;    // its tile grid and tile extents (grid = pcx * pcy CTAs)
+  int pcx, pcy, ptx, pty;    // its tile grid over a band and tile extents (grid = pcx * pcy CTAs)
+  int pband;                 // bands along x, marched one after another
+  int pband_req;             // requested band count (0: automatic)
   int pnt;                   // its threads per CTA
   size_t psmem;              // its dynamic shared memory
   unsigned launch_no;        // launches so far (tags the progress counters)
@@ -1069,6 +1104,15 @@ void occupancy_aa(int* psi_occ, int* collide_occ) {
 
 bool plan_persist(sc_lbm* h);
 
+// The handle's launch description after a persistent plan.
+void apply_persist(sc_lbm* h) {
+  h->grid = h->pcx * h->pcy;
+  h->zmax = h->p.nz;
+  h->lay.tx = h->ptx;
+  h->lay.ty = h->pty;
+  if (h->withhold >= h->grid) h->withhold = -1;
+}
+
 // Grids of the in-place step: every resident CTA slot, the collision's at most
 // the evaporated-mass slots.
 int plan_aa(sc_lbm* h) {
@@ -1100,12 +1144,7 @@ int plan_aa(sc_lbm* h) {
     h->persist = plan_persist(h);
     if (!h->persist && h->p.staging == SC_STAGING_PERSISTENT)
       return fail(SC_EINVAL, "the persistent in-place step is not available here: %s", h->persist_why);
-    if (h->persist) {
-      h->grid = h->pcx * h->pcy;
-      h->zmax = h->p.nz;
-      h->lay.tx = h->ptx;
-      h->lay.ty = h->pty;
-    }
+    if (h->persist) apply_persist(h);
   }
   return SC_OK;
 }
@@ -1122,16 +1161,42 @@ void* persist_kernel(int storage, int nt) {
   }
 }
 
-// Tile grid of the persistent in-place step: cx x cy tile columns, one resident CTA
-// each (a cooperative launch), chosen to minimise the busiest SM's work per plane
-// (its CTAs' collisions plus their halo Psi, about a third of a collision per halo
-// cell), counting a single CTA per SM (8 warps) as three quarters as efficient as
-// two. Tiles narrower than 2 sites (the ragged last tile included) are allowed only
+// Tile grid of the persistent in-place step over a band: cx x cy tile columns, one
+// resident CTA each (a cooperative launch), chosen to minimise the busiest SM's work
+// per plane in warp rounds (its CTAs' collisions plus the Psi of their tiles and
+// halos, about a third of a collision per cell), counting a single CTA per SM (8
+// warps) as three quarters as efficient as two. Tiles narrower than 2 sites (the ragged last tile included) are allowed only
 // when one tile spans the axis, so that every slot a CTA reads for its halo belongs
 // to a direct neighbour. Returns false when no grid fits (the two-pass step is used
 // then).
+// Steps per persistent launch: at most kPersistMaxSteps, and few enough that the
+// launch's counters (K B (nz + 2) values) stay below 2^32.
+int persist_max_steps(const sc_lbm* h) {
+  const long long per_step = (long long)h->pband * (h->p.nz + 2);
+  return (int)std::max(1LL, std::min<long long>(kPersistMaxSteps, 4294967294LL / per_step));
+}
+
+bool plan_persist_bands(sc_lbm* h, int B);
+
+// The persistent step's plan: the requested band count, or the fewest bands (powers
+// of two dividing nx into bands of at least 2 sites) for which a tile grid fits.
+// More bands keep a band's plane in the L2 between its two reads (at 512^3 FP32 one
+// band reads 1.88x the algorithmic bytes from DRAM), but at 512^3 their smaller tiles
+// and extra plane handshakes cost more than that saves (1 / 2 / 4 bands: 11.8k /
+// 10.9k / 8.2k MLUPS); bands make the step possible where one band's tiles would not
+// fit the shared ring (planes of 2^20 sites).
 bool plan_persist(sc_lbm* h) {
+  if (h->pband_req > 0) return plan_persist_bands(h, h->pband_req);
+  for (int B = 1; B <= h->p.nx / 2 || B == 1; B *= 2) {
+    if (h->p.nx % B != 0) break;
+    if (plan_persist_bands(h, B)) return true;
+  }
+  return false;
+}
+
+bool plan_persist_bands(sc_lbm* h, int B) {
   const sc_params* p = &h->p;
+  const int bw = p->nx / B;  // the band width: tiles cover [b bw, (b + 1) bw)
   int dev = 0, sms = 1, coop = 0, smem_optin = 0;
   h->persist_why = "the device query failed";
   if (cudaGetDevice(&dev) != cudaSuccess) return false;
@@ -1159,13 +1224,13 @@ bool plan_persist(sc_lbm* h) {
       cudaGetLastError();
       continue;
     }
-    for (int cx = 1; cx <= p->nx && cx <= cap; ++cx) {
-      const int tx = (p->nx + cx - 1) / cx, cxr = (p->nx + tx - 1) / tx;
+    for (int cx = 1; cx <= bw && cx <= cap; ++cx) {
+      const int tx = (bw + cx - 1) / cx, cxr = (bw + tx - 1) / tx;
       if (cxr != cx) continue;  // the same tiles as a smaller cx
       // a halo site's arrived populations lie up to two sites from the tile: every tile,
       // the ragged last one included, must be at least 2 wide so they belong to a direct
       // neighbour (or to the tile itself)
-      if (cxr > 1 && p->nx - (cxr - 1) * tx < 2) continue;
+      if (cxr > 1 && bw - (cxr - 1) * tx < 2) continue;
       for (int cy = 1; cy <= p->ny && (long long)cx * cy <= cap; ++cy) {
         const int ty = (p->ny + cy - 1) / cy, cyr = (p->ny + ty - 1) / ty;
         if (cyr != cy) continue;
@@ -1179,16 +1244,17 @@ bool plan_persist(sc_lbm* h) {
         }
         const long long C = (long long)cx * cy;
         if (occ < 1 || C > (long long)occ * sms) continue;
-        // rounds of NT-thread work per plane on the busiest SM (collisions, plus halo Psi
-        // at about a third of a collision), counting an SM with fewer than 16 resident
-        // warps as three quarters as efficient
+        // warp rounds per plane on the busiest SM (collisions, plus the Psi of tile and
+        // halo at about a third of a collision): the CTAs of an SM share its issue slots,
+        // so a partly filled round costs its warps, not the whole CTA; an SM with fewer
+        // than 16 resident warps counts as three quarters as efficient
         const long long per_sm = (C + sms - 1) / sms;
-        const double rounds = std::ceil((double)tx * ty / nt) + 0.35 * std::ceil((double)(tx + 2) * (ty + 2) / nt);
-        const double cost = (double)per_sm * rounds * nt / (per_sm * nt >= 512 ? 1.0 : 0.75);
+        const double rounds = std::ceil((double)tx * ty / 32) + 0.35 * std::ceil((double)(tx + 2) * (ty + 2) / 32);
+        const double cost = (double)per_sm * rounds / (per_sm * nt >= 512 ? 1.0 : 0.75);
         if (cost < best * (1.0 - 1e-9)) {
           best = cost;
           found = true;
-          h->pcx = cx; h->pcy = cy; h->ptx = tx; h->pty = ty; h->psmem = smem; h->pnt = nt;
+          h->pcx = cx; h->pcy = cy; h->ptx = tx; h->pty = ty; h->psmem = smem; h->pnt = nt; h->pband = B;
         }
       }
     }
@@ -1201,6 +1267,9 @@ template <class S>
 cudaError_t launch_persist_t(sc_lbm* h, int K, cudaStream_t st) {
   AAPersist a{};
   a.cx = h->pcx; a.cy = h->pcy; a.TX = h->ptx; a.TY = h->pty;
+  a.B = h->pband;
+  a.bw = h->p.nx / h->pband;
+  a.edge = h->psi();  // the two-pass step's Psi array (np >= B nz ny entries), unused here
   a.K = K;
   a.odd0 = h->cur;
   a.epoch = (unsigned long long)(++h->launch_no) << 32;
@@ -1599,7 +1668,7 @@ int sc_lbm_step(sc_lbm* h, int64_t nsteps) {
   int64_t left = nsteps;
   if (h->persist) {
     while (left > 0) {
-      const int k = (int)std::min<int64_t>(left, kPersistMaxSteps);
+      const int k = (int)std::min<int64_t>(left, persist_max_steps(h));
       int rc = launch_persist(h, k, h->stream);
       if (rc) return rc;
       left -= k;
@@ -1976,7 +2045,7 @@ int sc_slab_unpack(sc_lbm* h, int32_t side, const void* in_dev) {
 int sc_lbm_launch_count(sc_lbm* h, int64_t nsteps, int64_t* launches) {
   if (!h || !launches) return fail(SC_EINVAL, "NULL argument");
   if (nsteps < 0) return fail(SC_EINVAL, "nsteps must be >= 0");
-  if (h->persist) *launches = (nsteps + kPersistMaxSteps - 1) / kPersistMaxSteps;
+  if (h->persist) *launches = (nsteps + persist_max_steps(h) - 1) / persist_max_steps(h);
   else *launches = h->lay.aa ? 2 * nsteps : nsteps;
   return SC_OK;
 }
@@ -1995,6 +2064,28 @@ int sc_lbm_set_wait(sc_lbm* h, int64_t limit_ns, int32_t withhold_cta) {
     return fail(SC_EINVAL, "withhold_cta out of range");
   h->wait_limit_ns = limit_ns;
   h->withhold = withhold_cta;
+  return SC_OK;
+}
+
+int sc_lbm_persist_bands(sc_lbm* h, int32_t request, int32_t* bands) {
+  if (!h) return fail(SC_EINVAL, "NULL handle");
+  if (request < -1) return fail(SC_EINVAL, "request must be -1, 0 or a band count");
+  if (request >= 0) {
+    if (!h->persist) return fail(SC_EINVAL, "the lattice does not use the persistent in-place step");
+    if (request > 1 && (h->p.nx % request != 0 || h->p.nx / request < 2))
+      return fail(SC_EINVAL, "%d bands must divide nx = %d into bands of at least 2 sites", request, h->p.nx);
+    const int old = h->pband_req;
+    h->pband_req = request;
+    if (!plan_persist(h)) {
+      const char* why = h->persist_why;
+      h->pband_req = old;
+      plan_persist(h);  // the previous plan, which fitted
+      apply_persist(h);
+      return fail(SC_EINVAL, "no persistent plan with %d bands: %s", request, why);
+    }
+    apply_persist(h);
+  }
+  if (bands) *bands = h->persist ? h->pband : 0;
   return SC_OK;
 }
 

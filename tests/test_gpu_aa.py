@@ -1,6 +1,7 @@
 """The in-place (AA) layout: the time step of Sec. II on one population lattice
 updated in place, by either of its two kernels: the persistent cooperative step
-(one launch for many steps, CTAs ordered by bounded neighbour waits) or the
+(one launch for many steps, CTAs ordered by bounded neighbour waits, the lattice
+marched whole or in x-bands one after another) or the
 two-pass step (Psi of every site, then stream + sink + force + collision). The
 state either reaches after any number of steps -- in either of its two storage
 forms -- is the two-lattice step's, bit for bit, for every storage type, geometry
@@ -56,10 +57,13 @@ CASES = _cases()
 STAGINGS = ["persistent", "thread"]
 
 
-def _run(sc, params, init, steps, layout, staging="auto"):
+def _run(sc, params, init, steps, layout, staging="auto", bands=None):
     lat = sc.Lattice(dict(params, layout=layout, staging=staging if layout == "aa" else "auto"))
     if layout == "aa" and staging == "persistent":
         assert lat.launch_info()["staging"] == "persistent"
+    if bands is not None:
+        assert lat.persist_bands(bands) == bands
+        assert lat.launch_info()["bands"] == bands
     lat.init(init)
     out = []
     done = 0
@@ -93,6 +97,46 @@ def test_same_bits_as_two_lattices(sc, case, storage, staging):
         assert np.array_equal(fa, ft), (case, storage, n)
         assert np.array_equal(ra, rt) and np.array_equal(ba, bt), (case, storage, n)
         _same_diag(da, dt)
+
+
+# band counts dividing each case's nx (bands of 2 sites included)
+BANDS = {"seam_sink_unequal_tau": [2, 4, 16], "periodic_two_segments": [2, 5, 65],
+         "self_couplings_sphere_sink": [2, 5, 10], "film_wall_sink": [2]}
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+@pytest.mark.parametrize("case,bands", [(c, b) for c, bs in BANDS.items() for b in bs])
+def test_bands_same_bits_as_two_lattices(sc, case, bands, storage):
+    """The persistent step marching the lattice in x-bands, one after another (halo
+    Psi at a band edge saved by the band before or formed from the band after), gives
+    the two-lattice step's bits."""
+    params, init = CASES[case]
+    params = dict(params, storage=storage)
+    steps = [1, 2, 7, 77]
+    aa = _run(sc, params, init, steps, "aa", "persistent", bands=bands)
+    two = _run(sc, params, init, steps, "two")
+    for n, (fa, (ra, ba), da), (ft, (rt, bt), dt) in zip(steps, aa, two):
+        assert np.array_equal(fa, ft), (case, bands, storage, n)
+        assert np.array_equal(ra, rt) and np.array_equal(ba, bt), (case, bands, storage, n)
+        _same_diag(da, dt)
+
+
+def test_band_requests(sc):
+    params, init = CASES["seam_sink_unequal_tau"]
+    lat = sc.Lattice(dict(params, layout="aa", staging="persistent"))
+    assert lat.persist_bands() == 1  # a 32^2 plane is far below the automatic limit
+    for bad in (3, 33, -2):  # not a divisor of nx = 32, bands under 2 sites, no such request
+        with pytest.raises(sc.ScError, match="-1"):
+            lat.persist_bands(bad)
+    assert lat.persist_bands() == 1
+    assert lat.persist_bands(8) == 8 and lat.launch_info()["tile_x"] <= 4
+    assert lat.persist_bands(0) == 1
+    lat.close()
+    lat = sc.Lattice(dict(params, layout="aa", staging="thread"))
+    assert lat.persist_bands() == 0
+    with pytest.raises(sc.ScError, match="-1"):
+        lat.persist_bands(2)
+    lat.close()
 
 
 @pytest.mark.parametrize("staging", STAGINGS)
@@ -182,11 +226,18 @@ def test_launch_info_and_tuner_report_the_in_place_step(sc):
     big = dict(params, nx=512, ny=256, nz=4)
     lat = sc.Lattice(dict(big, layout="aa"))
     info = lat.launch_info()
-    assert info["staging"] == "persistent" and info["zchunk"] == big["nz"]
+    assert info["staging"] == "persistent" and info["zchunk"] == big["nz"] and info["bands"] == 1
     cols = -(-big["nx"] // info["tile_x"]) * -(-big["ny"] // info["tile_y"])
     assert info["ctas"] == cols
     assert lat.launch_count(10) == 1 and lat.launch_count(2049) == 3
     lat.close()
+    # one band while its tiles fit the shared ring (512^2), two where they do not (1024^2)
+    for n, bands in ((512, 1), (1024, 2)):
+        lat = sc.Lattice(dict(big, nx=n, ny=n, nz=2, layout="aa"))
+        info = lat.launch_info()
+        assert info["staging"] == "persistent" and info["bands"] == bands, n
+        assert info["ctas"] == -(-n // bands // info["tile_x"]) * -(-n // info["tile_y"])
+        lat.close()
 
 
 def test_batch_rejects_in_place_members(sc):
@@ -206,10 +257,12 @@ def test_full_size_droplet_same_bits(sc, n):
     from paper_1701_03637_gb300.workloads import droplet
     params, init = droplet(n, 24.0 * n / 128, 1)
     fields = {}
-    for kind in ("aa", "aa_thread", "two"):
+    for kind in ("aa", "aa_bands", "aa_thread", "two"):
         layout = "two" if kind == "two" else "aa"
-        staging = {"aa": "persistent", "aa_thread": "thread", "two": "auto"}[kind]
+        staging = {"aa": "persistent", "aa_bands": "persistent", "aa_thread": "thread", "two": "auto"}[kind]
         lat = sc.Lattice(dict(params, layout=layout, staging=staging))
+        if kind == "aa_bands":
+            assert lat.persist_bands(4) == 4
         lat.init(init)
         lat.step(9)
         f9 = lat.read_fields_device().clone()
@@ -218,7 +271,7 @@ def test_full_size_droplet_same_bits(sc, n):
         fields[kind] = (f9, f20, lat.diagnostics())
         lat.close()
         torch.cuda.synchronize()
-    for kind in ("aa", "aa_thread"):
+    for kind in ("aa", "aa_bands", "aa_thread"):
         for k in (0, 1):
             assert torch.equal(fields[kind][k], fields["two"][k]), (kind, k)
         _same_diag(fields[kind][2], fields["two"][2])

@@ -20,13 +20,16 @@ def sc():
     return mod
 
 
+@pytest.mark.parametrize("bands", [1, 4])
 @pytest.mark.parametrize("withhold", [0, "last"])
-def test_withheld_progress_gives_etimeout_and_the_device_stays_usable(sc, withhold):
+def test_withheld_progress_gives_etimeout_and_the_device_stays_usable(sc, withhold, bands):
     from paper_1701_03637_gb300.workloads import droplet
     params, init = droplet(48, 9.0, 7)
     lat = sc.Lattice(dict(params, layout="aa", staging="persistent"))
+    assert lat.persist_bands(bands) == bands
     info = lat.launch_info()
-    assert info["staging"] == "persistent" and info["ctas"] >= 9
+    # one band: a 3 x 3 or larger tile grid; four bands of 12 sites: a few CTAs
+    assert info["staging"] == "persistent" and info["ctas"] >= (9 if bands == 1 else 2)
     cta = info["ctas"] - 1 if withhold == "last" else withhold
     lat.init(init)
     lat.set_wait(50_000_000, cta)
