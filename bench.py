@@ -191,6 +191,10 @@ def arm_config(args, world):
                 "l2": l2_note(sum(population_bytes(p, args.storage, "two") for p, _ in members)),
                 "parallelism": "one persistent launch per step over all members"
                                + (f"; members split over {world} ranks by size, no data exchange" if world > 1 else "")}
+    if args.workload == "ncomp3_128":
+        return {"workload": NCOMP_DESC, "sites": 128 ** 3, "components": 3, "storage": "f32", "layout": "two",
+                "l2": l2_note(128 ** 3 * 3 * 19 * 4 * 2),
+                "parallelism": f"independent replicas x{world}"}
     if args.workload == "serve":
         storage = args.storage if args.storage != "f32" else "f16"
         return {"workload": serve_desc(args, storage), "requests": args.requests, "rate_per_s": args.rate,
@@ -397,6 +401,18 @@ def run_reference(args):
         return
     import oracle
     world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.workload == "ncomp3_128":
+        rate, steps = ncomp_oracle_rate(max(5.0, min(120.0, 0.5 * (args.steps + args.warmup))))
+        sample = (f"the N-component FP64 oracle (numpy, one thread) on the 24^3 three-component droplet of the "
+                  f"same recipe (radius 4.5), {steps} steps")
+        out = {"metric": "MLUPS", "value": rate, "unit": "MLUPS", "impl": "reference", "n_gpus": args.gpus,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": 24 ** 3 / rate / 1e3,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+               "data": "synthetic", "config": arm_config(args, world), "sample_sites": 24 ** 3,
+               "cpu_baseline": {"value": rate, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+               "e2e": {"value": rate, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(out))
+        return
     lattices, sample, label = reference_lattices(args)
     cores = host_cores()
     oracle.set_threads(cores)
@@ -1001,10 +1017,103 @@ def run_slab(args):
         dist.destroy_process_group()
 
 
+NCOMP_DESC = ("ncomp3_128: three-component D3Q19 Shan-Chen (Eq. (3) summed over the other components), 128^3 "
+              "periodic, droplet of component 0 (radius 24, 0.7 / 0.04) in component 1, component 2 at 0.1 "
+              "throughout, g01 = 3.6, g02 = g12 = 1.0, tau = 1, f32 populations, two lattices")
+
+
+def ncomp_oracle_rate(budget_s):
+    """The N-component FP64 oracle (numpy, as it stands) on a 24^3 sample of the
+    ncomp3 recipe: MLUPS over whole-lattice steps, and the steps taken."""
+    import numpy as np
+
+    from oracle import multi
+    from paper_1701_03637_gb300.workloads import three_component_droplet
+    p, rho = three_component_droplet(24, 4.5, 1)
+    o = multi.Lattice(p["nx"], p["ny"], p["nz"], p["tau"], p["g"])
+    o.set_populations(multi.W[None, :, None, None, None] * rho[:, None].astype(np.float64))
+    t = time.perf_counter()
+    o.step(1)
+    one = time.perf_counter() - t
+    steps = max(1, int(budget_s / max(one, 1e-6)))
+    t = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t
+    return 24 ** 3 * steps / dt / 1e6, steps
+
+
+def run_ncomp(args):
+    """More than two components (sc_ncomp_*): three components at 128^3, two launches
+    per step (Psi of every site, then pull + force + shifted collision); independent
+    replicas under torchrun."""
+    import torch
+    import torch.distributed as dist
+
+    import paper_1701_03637_gb300 as sc
+    from paper_1701_03637_gb300.ncomp import NLattice
+    from paper_1701_03637_gb300.workloads import three_component_droplet
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    sc.build()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    params, rho = three_component_droplet(128, 24.0, 1)
+    nc = len(params["tau"])
+    n = params["nx"] * params["ny"] * params["nz"]
+    lat = NLattice(**params)
+    lat.init_fields(rho)
+    lat.step(args.warmup)
+    lat.sync()
+    sampler = ClockSampler()
+    time.sleep(0.3)
+    t0 = time.time()
+    ms = timed_steps(lat, args.steps, lat.stream, barrier)
+    t1 = time.time()
+    sampler.stop()
+    ms_max = max_over_ranks(ms, world, "cuda")
+    value = replica_value(n, args.steps, world, ms_max)
+    peak, peak_kind = measured_peak_hbm()
+    per_site = nc * BYTES_PER_SITE["f32"] // 2  # every population of every component read and written once
+    achieved = per_site * n / (ms * 1e-3 / args.steps) / 1e9
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, steps = ncomp_oracle_rate(10.0)
+        cpu = {"value": rate, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+               "sample": f"the N-component FP64 oracle (numpy, one thread) on the 24^3 three-component droplet "
+                         f"of the same recipe (radius 4.5), {steps} steps"}
+    if rank == 0:
+        out = {"metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "config": arm_config(args, world),
+               "launch": {"kernels": "k_n_psi + k_n_collide", "threads": 256, "components": nc},
+               "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                            "frac": achieved / peak, "traffic": None,
+                            "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                            "algorithmic_bytes_per_site": per_site,
+                            "kernel": "k_n_psi + k_n_collide (one step, two launches)"},
+               "cpu_baseline": cpu, "e2e": None, "gpu_launches": 2 * args.steps,
+               "clocks": sampler.summary(t0, t1)}
+        print(json.dumps(out))
+    lat.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "ncomp3_128":
+        run_ncomp(args)
     elif args.layout == "slab":
         run_slab(args)
     elif args.workload == "ensemble_64":

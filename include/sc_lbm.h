@@ -343,6 +343,10 @@ void sc_ncomp_destroy(sc_ncomp* h);
 /* Canonical populations f[c][i][s] (ncomp * 19 * nx*ny*nz doubles, converted to FP32);
    solid sites are ignored. Synchronous. */
 int sc_ncomp_write_populations(sc_ncomp* h, const double* f_host);
+/* Rest populations w_i rho^c (Eq. 2 at u = 0) from caller density fields rho[c][s]
+   (ncomp * nx*ny*nz floats, x fastest); solid sites are ignored. Resets the step
+   count. Synchronous. */
+int sc_ncomp_init_fields(sc_ncomp* h, const float* rho_host);
 /* Canonical populations out (same layout; 0 at solid sites). Synchronous. */
 int sc_ncomp_read_populations(sc_ncomp* h, double* f_host);
 /* Advance nsteps steps (asynchronous, two launches per step). */

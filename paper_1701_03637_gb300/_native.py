@@ -132,6 +132,7 @@ _SIGS = {
     "sc_ncomp_create": (C.c_int, [C.POINTER(NParams), _VP, C.POINTER(_VP)]),
     "sc_ncomp_destroy": (None, [_VP]),
     "sc_ncomp_write_populations": (C.c_int, [_VP, _VP]),
+    "sc_ncomp_init_fields": (C.c_int, [_VP, _VP]),
     "sc_ncomp_read_populations": (C.c_int, [_VP, _VP]),
     "sc_ncomp_step": (C.c_int, [_VP, C.c_int64]),
     "sc_ncomp_sync": (C.c_int, [_VP]),

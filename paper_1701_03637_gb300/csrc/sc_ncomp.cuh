@@ -173,12 +173,29 @@ __global__ void k_n_load(const NDev D, const float* __restrict__ in, float* __re
   }
 }
 
+// Rest populations w_i rho^c (Eq. 2 at u = 0) of densities rho[c][s] (dense) into
+// out[c][i][s] (dense), the canonical form k_n_load places.
+template <int NC>
+__global__ void k_n_rest(const NDev D, const float* __restrict__ rho, float* __restrict__ out) {
+  const LatDev& L = D.L;
+  const long long n = (long long)L.nxny * L.nz;
+  for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const float r = rho[c * n + s];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) out[((long long)c * Q + i) * n + s] = rest_pop(i, r);
+    }
+  }
+}
+
 template <int NC>
 cudaError_t n_launch(int what, const NDev& D, const float* a, float* b, float* c, int grid, cudaStream_t st) {
   switch (what) {
     case 0: k_n_psi<NC><<<grid, 256, 0, st>>>(D, a, b); break;
     case 1: k_n_collide<NC><<<grid, 256, 0, st>>>(D, a, b, c); break;
     case 2: k_n_canonical<NC><<<grid, 256, 0, st>>>(D, a, b); break;
+    case 4: k_n_rest<NC><<<grid, 256, 0, st>>>(D, a, b); break;
     default: k_n_load<NC><<<grid, 256, 0, st>>>(D, a, b); break;
   }
   return cudaGetLastError();
@@ -278,6 +295,21 @@ int sc_ncomp_write_populations(sc_ncomp* h, const double* f) {
   CK(cudaMemcpyAsync(stage, tmp.data(), sizeof(float) * m, cudaMemcpyHostToDevice, h->stream));
   CK(n_dispatch(h->p.ncomp, 3, h->D, stage, h->pop(h->cur), nullptr, h->grid, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  return SC_OK;
+}
+
+int sc_ncomp_init_fields(sc_ncomp* h, const float* rho) {
+  Range range("sc_ncomp_init_fields");
+  if (!h || !rho) return fail(SC_EINVAL, "NULL argument");
+  const size_t n = (size_t)h->p.nx * h->p.ny * h->p.nz;
+  // densities into the Psi array (ncomp * np >= ncomp * n floats), their rest
+  // populations into the other buffer, then placed where the next pull reads them
+  float* stage = h->pop(1 - h->cur);
+  CK(cudaMemcpyAsync(h->psi(), rho, sizeof(float) * h->p.ncomp * n, cudaMemcpyHostToDevice, h->stream));
+  CK(n_dispatch(h->p.ncomp, 4, h->D, h->psi(), stage, nullptr, h->grid, h->stream));
+  CK(n_dispatch(h->p.ncomp, 3, h->D, stage, h->pop(h->cur), nullptr, h->grid, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  h->step = 0;
   return SC_OK;
 }
 

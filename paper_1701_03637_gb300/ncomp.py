@@ -49,6 +49,12 @@ class NLattice:
         assert f.size == self.ncomp * Q * self.n
         check(load().sc_ncomp_write_populations(self._h, f.ctypes.data))
 
+    def init_fields(self, rho) -> None:
+        """Rest populations w_i rho^c from densities rho[c][z][y][x] (computed on the device)."""
+        rho = np.ascontiguousarray(rho, np.float32).reshape(-1)
+        assert rho.size == self.ncomp * self.n
+        check(load().sc_ncomp_init_fields(self._h, rho.ctypes.data))
+
     def read_populations(self) -> np.ndarray:
         f = np.empty(self.ncomp * Q * self.n, np.float64)
         check(load().sc_ncomp_read_populations(self._h, f.ctypes.data))

@@ -37,6 +37,25 @@ def droplet(n, radius, seed, rho_hi=1.0, rho_lo=0.03, rho_H=0.03, noise=1e-4, st
     return params, init
 
 
+def three_component_droplet(n, radius, seed, rho_hi=0.7, rho_lo=0.04, rho_third=0.1, noise=1e-4):
+    """Three components in an n^3 periodic box: a droplet of component 0 (rho_hi inside
+    the sphere, rho_lo outside) in component 1 (the complement), with component 2
+    dissolved everywhere at rho_third; uniform noise of +-noise on every density
+    (numpy's PCG64 with `seed`). g^{01} = 3.6 (the paper's G), g^{02} = g^{12} = 1.0,
+    no self coupling, tau = 1. Returns (NLattice keyword arguments, rho[c][z][y][x])."""
+    c = (n - 1) / 2.0
+    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    inside = (x - c) ** 2 + (y - c) ** 2 + (z - c) ** 2 <= radius * radius
+    rho = np.empty((3, n, n, n), np.float32)
+    rho[0] = np.where(inside, rho_hi, rho_lo)
+    rho[1] = np.where(inside, rho_lo, rho_hi)
+    rho[2] = rho_third
+    rng = np.random.default_rng(seed)
+    rho += rng.uniform(-noise, noise, rho.shape).astype(np.float32)
+    g = [[0.0, 3.6, 1.0], [3.6, 0.0, 1.0], [1.0, 1.0, 0.0]]
+    return dict(nx=n, ny=n, nz=n, tau=[1.0, 1.0, 1.0], g=g), rho
+
+
 WORKLOADS = {
     "film_4x4x128": lambda **kw: film_4x4x128(**kw),
     "droplet_128": lambda **kw: droplet(128, 24.0, 1, **kw),

@@ -99,3 +99,29 @@ def test_invalid_parameters(sc):
         g = args["g"] if args["g"].shape[0] >= len(args["tau"]) else np.zeros((len(args["tau"]),) * 2)
         with pytest.raises(sc.ScError, match="-1"):
             NLattice(4, 4, 4, args["tau"], g)
+
+
+def test_init_fields_gives_rest_populations(sc):
+    """sc_ncomp_init_fields: populations w_i rho^c (Eq. 2 at rest) of the given
+    densities, FP32-rounded, solid sites 0; one step from there matches the oracle."""
+    from oracle import multi
+    from paper_1701_03637_gb300.ncomp import NLattice
+    from paper_1701_03637_gb300.workloads import three_component_droplet
+    params, rho = three_component_droplet(12, 3.0, 4)
+    lat = NLattice(**params, wall_z0=5, wall_thickness=2)
+    lat.init_fields(rho)
+    f = lat.read_populations()
+    want = multi.W[None, :, None, None, None] * rho[:, None].astype(np.float64)
+    solid = np.zeros(rho.shape[1:], bool)
+    solid[5:7] = True
+    want[:, :, solid] = 0.0
+    assert np.all(np.abs(f - want) <= 1.2e-7 * np.abs(want)), np.max(np.abs(f - want))
+    o = multi.Lattice(12, 12, 12, params["tau"], params["g"], wall_z0=5, wall_thickness=2)
+    o.set_populations(f)
+    lat.step(1)
+    o.step(1)
+    fo = o.f
+    den = np.maximum(np.maximum(np.abs(fo), multi.W[None, :, None, None, None] * np.abs(fo).sum(axis=1, keepdims=True)),
+                     1e-30)
+    assert np.max(np.abs(lat.read_populations() - fo) / den) < 1e-6
+    lat.close()
