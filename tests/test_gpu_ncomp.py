@@ -115,7 +115,9 @@ def test_init_fields_gives_rest_populations(sc):
     solid = np.zeros(rho.shape[1:], bool)
     solid[5:7] = True
     want[:, :, solid] = 0.0
-    assert np.all(np.abs(f - want) <= 1.2e-7 * np.abs(want)), np.max(np.abs(f - want))
+    # the library's FP32 weights sum to 1 exactly (w_1 = 1/18 - 1 ulp, w_0 = 1 - 12 w_1),
+    # so w_0 is 1.2e-7 above 1/3; with the product's rounding (2^-24) the bound is 2.5e-7
+    assert np.all(np.abs(f - want) <= 2.5e-7 * np.abs(want)), np.max(np.abs(f - want) / np.maximum(want, 1e-30))
     o = multi.Lattice(12, 12, 12, params["tau"], params["g"], wall_z0=5, wall_thickness=2)
     o.set_populations(f)
     lat.step(1)
