@@ -1043,8 +1043,8 @@ def ncomp_oracle_rate(budget_s):
 
 
 def run_ncomp(args):
-    """More than two components (sc_ncomp_*): three components at 128^3, two launches
-    per step (Psi of every site, then pull + force + shifted collision); independent
+    """More than two components (sc_ncomp_*): three components at 128^3, one launch per
+    step (tile columns marching plane chunks, Psi in a shared ring); independent
     replicas under torchrun."""
     import torch
     import torch.distributed as dist
@@ -1094,13 +1094,13 @@ def run_ncomp(args):
                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                "config": arm_config(args, world),
-               "launch": {"kernels": "k_n_psi + k_n_collide", "threads": 256, "components": nc},
+               "launch": {"kernels": "k_n_step", "threads": 256, "components": nc},
                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                             "frac": achieved / peak, "traffic": None,
                             "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
                             "algorithmic_bytes_per_site": per_site,
-                            "kernel": "k_n_psi + k_n_collide (one step, two launches)"},
-               "cpu_baseline": cpu, "e2e": None, "gpu_launches": 2 * args.steps,
+                            "kernel": "k_n_step (one launch per step)"},
+               "cpu_baseline": cpu, "e2e": None, "gpu_launches": args.steps,
                "clocks": sampler.summary(t0, t1)}
         print(json.dumps(out))
     lat.close()

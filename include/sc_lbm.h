@@ -322,9 +322,10 @@ int sc_slab_unpack(sc_lbm* h, int32_t side, const void* in_dev);
    relaxation time tau[c]; g[c][cbar] is the coupling g^{c cbar} of Eq. (3) (the diagonal
    the self couplings). The common velocity is u' = sum_c (m^c / tau_c) /
    sum_c (rho^c / tau_c) and the shift tau_c F^c / rho^c, as for two components. FP32
-   populations, two lattices, two launches per step (Psi of every component and site,
-   then pull + force + collision). With two components and non-zero self couplings the
-   populations are bit-identical to sc_lbm_step's. */
+   populations, two lattices, one launch per step (tile columns of 32 x 8 sites marching
+   chunks of planes, Psi of every component in a shared ring, then pull + force +
+   collision). With two components and non-zero self couplings the populations are
+   bit-identical to sc_lbm_step's. */
 #define SC_MAX_COMP 4
 
 typedef struct sc_nparams {
@@ -349,7 +350,7 @@ int sc_ncomp_write_populations(sc_ncomp* h, const double* f_host);
 int sc_ncomp_init_fields(sc_ncomp* h, const float* rho_host);
 /* Canonical populations out (same layout; 0 at solid sites). Synchronous. */
 int sc_ncomp_read_populations(sc_ncomp* h, double* f_host);
-/* Advance nsteps steps (asynchronous, two launches per step). */
+/* Advance nsteps steps (asynchronous, one launch per step). */
 int sc_ncomp_step(sc_ncomp* h, int64_t nsteps);
 int sc_ncomp_sync(sc_ncomp* h);
 

@@ -6,13 +6,15 @@
 //
 // Periodic lattice with an optional solid slab (halfway bounce-back, Psi = 0 at
 // solid sites); no evaporation sink (the paper states it for two components).
-// Two population lattices of FP32 arrays f[c][i][s]; each step is two launches:
-// k_n_psi forms Psi^c of every site from its pulled populations into an FP32 array
-// Psi[c][s], then k_n_collide pulls again, forms every component's force from the
-// Psi array, the common velocity and the shifted relaxation, and stores f*. The
-// per-component arithmetic is the two-component kernels' (sum19, psi_of, momentum,
-// force_sum_one = force_sums per component, relax_core), and the sums over
-// components are ordered so that two components give their bits.
+// Two population lattices of FP32 arrays f[c][i][s]; each step is one launch of
+// k_n_step: a CTA of 32 x 8 threads owns a tile column and a chunk of its planes and
+// marches them, forming Psi^c of plane p + 1 over the tile and a one-site halo from
+// the pulled populations into a shared ring of 4 planes, then pulling plane p again
+// (an L2 hit), forming every component's force from the ring, the common velocity
+// and the shifted relaxation, and storing f*. The per-component arithmetic is the
+// two-component kernels' (sum19, psi_of, momentum, force_sum_one = force_sums per
+// component, relax_core), and the sums over components are ordered so that two
+// components give their bits.
 
 namespace {
 
@@ -35,93 +37,121 @@ __device__ __forceinline__ void pull_comp(const LatDev& L, const float* __restri
   });
 }
 
+constexpr int kNTX = 32, kNTY = 8, kNT = kNTX * kNTY;  // tile of the N-component step
+constexpr int kNRW = kNTX + 2, kNRH = kNTY + 2;         // with its one-site halo
+
+// Psi^c of 4 rolling planes (slot q & 3) over a tile and its halo.
 template <int NC>
-__global__ void __launch_bounds__(256) k_n_psi(const NDev D, const float* __restrict__ src, float* __restrict__ psi) {
+struct NRing {
+  float v[4][NC][kNRH][kNRW];
+};
+
+// Psi of every component of plane q (any integer; periodic) over the tile at (x0, y0)
+// and its halo into ring slot q & 3.
+template <int NC>
+__device__ __forceinline__ void n_psi_plane(const NDev& D, const float* __restrict__ src, NRing<NC>& r, int q,
+                                            int x0, int y0) {
   const LatDev& L = D.L;
-  const long long n = (long long)L.nxny * L.nz;
-  for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
-    int x, y, z;
-    site_of(L, s, x, y, z);
-    if (site_class(L, x, y, z) == SOLID) {
+  const int zq = wrapi(q, L.nz), sl = q & 3;
+  const bool solid = solid_z(L, zq);
+  for (int h = threadIdx.x; h < kNRH * kNRW; h += kNT) {
+    const int hx = h % kNRW, hy = h / kNRW;
+    if (solid) {
 #pragma unroll
-      for (int c = 0; c < NC; ++c) psi[c * L.np + s] = 0.f;
+      for (int c = 0; c < NC; ++c) r.v[sl][c][hy][hx] = 0.f;
       continue;
     }
-    const PullIdx P(L, x, y, z);
+    const int x = wrap_near(x0 + hx - 1, L.nx), y = wrap_near(y0 + hy - 1, L.ny);
+    const PullIdx P(L, x, y, zq);
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
       float f[Q];
       pull_comp(L, src + (long long)c * Q * L.np, P, f);
-      psi[c * L.np + s] = psi_of(sum19(f));
+      r.v[sl][c][hy][hx] = psi_of(sum19(f));
     }
   }
 }
 
+// Stream, force, common velocity and shifted relaxation of site (x, y, p) (tile cell
+// (tx, ty)), Psi from the ring; stores f*.
 template <int NC>
-__global__ void __launch_bounds__(256) k_n_collide(const NDev D, const float* __restrict__ src,
-                                                   float* __restrict__ dst, const float* __restrict__ psi) {
+__device__ __forceinline__ void n_collide_site(const NDev& D, const float* __restrict__ src, float* __restrict__ dst,
+                                               const NRing<NC>& r, int p, int x, int y, int tx, int ty) {
   const LatDev& L = D.L;
-  const long long n = (long long)L.nxny * L.nz;
-  for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
-    int x, y, z;
-    site_of(L, s, x, y, z);
-    if (site_class(L, x, y, z) == SOLID) continue;
-    const PullIdx P(L, x, y, z);
-    float f[NC][Q], rho[NC], m[NC][3];
+  const PullIdx P(L, x, y, p);
+  const int s = P.s;
+  float f[NC][Q], rho[NC], m[NC][3];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      pull_comp(L, src + (long long)c * Q * L.np, P, f[c]);
-      rho[c] = sum19(f[c]);
-      momentum(f[c], m[c]);
-    }
-    // u' = sum_c m^c om_c / sum_c rho^c om_c, summed from the last component down (the
-    // two-component kernels' order for NC = 2)
-    float den = __fmul_rn(rho[NC - 1], D.om[NC - 1]);
+  for (int c = 0; c < NC; ++c) {
+    pull_comp(L, src + (long long)c * Q * L.np, P, f[c]);
+    rho[c] = sum19(f[c]);
+    momentum(f[c], m[c]);
+  }
+  // u' = sum_c m^c om_c / sum_c rho^c om_c, summed from the last component down (the
+  // two-component kernels' order for NC = 2)
+  float den = __fmul_rn(rho[NC - 1], D.om[NC - 1]);
 #pragma unroll
-    for (int c = NC - 2; c >= 0; --c) den = __fmaf_rn(rho[c], D.om[c], den);
-    const float inv = den > 0.0f ? __fdiv_rn(1.0f, den) : 0.0f;
-    float up[3];
+  for (int c = NC - 2; c >= 0; --c) den = __fmaf_rn(rho[c], D.om[c], den);
+  const float inv = den > 0.0f ? __fdiv_rn(1.0f, den) : 0.0f;
+  float up[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    float num = __fmul_rn(m[NC - 1][d], D.om[NC - 1]);
+#pragma unroll
+    for (int c = NC - 2; c >= 0; --c) num = __fmaf_rn(m[c][d], D.om[c], num);
+    up[d] = __fmul_rn(num, inv);
+  }
+  // a^c = sum_i w_i Psi^c(x + e_i) e_i from the ring (planes p - 1, p, p + 1)
+  float a[NC][3];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    auto psi1 = [&](int sl, int yy, int xx) { return r.v[sl][c][yy + 1][xx + 1]; };
+    force_sum_one(psi1, (p - 1) & 3, p & 3, (p + 1) & 3, ty, tx, a[c]);
+  }
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    // A^c = sum_cbar g^{c cbar} a^cbar: the other components first (the first as a
+    // product, the rest as fused multiply-adds), the self coupling last
+    float A[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      float num = __fmul_rn(m[NC - 1][d], D.om[NC - 1]);
+      float acc = 0.0f;
+      bool first = true;
 #pragma unroll
-      for (int c = NC - 2; c >= 0; --c) num = __fmaf_rn(m[c][d], D.om[c], num);
-      up[d] = __fmul_rn(num, inv);
-    }
-    // a^c = sum_i w_i Psi^c(x + e_i) e_i from the Psi array (periodic neighbours)
-    const int nx = L.nx, ny = L.ny;
-    float a[NC][3];
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      const float* pc = psi + (long long)c * L.np;
-      auto psi1 = [&](int zb, int yy, int xx) {
-        yy = yy < 0 ? yy + ny : (yy >= ny ? yy - ny : yy);
-        xx = xx < 0 ? xx + nx : (xx >= nx ? xx - nx : xx);
-        return pc[zb + yy * nx + xx];
-      };
-      force_sum_one(psi1, P.zs[2], P.zs[1], P.zs[0], y, x, a[c]);
-    }
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      // A^c = sum_cbar g^{c cbar} a^cbar: the other components first (the first as a
-      // product, the rest as fused multiply-adds), the self coupling last
-      float A[3];
-#pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        float acc = 0.0f;
-        bool first = true;
-#pragma unroll
-        for (int cb = 0; cb < NC; ++cb) {
-          if (cb == c) continue;
-          acc = first ? __fmul_rn(D.g[c][cb], a[cb][d]) : __fmaf_rn(D.g[c][cb], a[cb][d], acc);
-          first = false;
-        }
-        A[d] = __fmaf_rn(D.g[c][c], a[c][d], acc);
+      for (int cb = 0; cb < NC; ++cb) {
+        if (cb == c) continue;
+        acc = first ? __fmul_rn(D.g[c][cb], a[cb][d]) : __fmaf_rn(D.g[c][cb], a[cb][d], acc);
+        first = false;
       }
-      relax_core(D.om[c], D.tau[c], f[c], rho[c], psi[c * L.np + s], 1.0f, A, up);
-#pragma unroll
-      for (int i = 0; i < Q; ++i) dst[((long long)c * Q + i) * L.np + s] = f[c][i];
+      A[d] = __fmaf_rn(D.g[c][c], a[c][d], acc);
     }
+    relax_core(D.om[c], D.tau[c], f[c], rho[c], r.v[p & 3][c][ty + 1][tx + 1], 1.0f, A, up);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) dst[((long long)c * Q + i) * L.np + s] = f[c][i];
+  }
+}
+
+// One step: CTA (column, chunk) marches planes [zb, ze) of its tile column, one
+// barrier per plane. Psi of plane p + 2 goes to ring slot (p + 2) & 3 while other
+// threads may still collide plane p (slots p - 1, p, p + 1); the barrier after it
+// is passed only when every thread has collided plane p.
+template <int NC>
+__global__ void __launch_bounds__(kNT) k_n_step(const NDev D, const float* __restrict__ src, float* __restrict__ dst,
+                                                int cols_x, int cols, int nch) {
+  __shared__ NRing<NC> r;
+  const LatDev& L = D.L;
+  const int col = (int)blockIdx.x % cols, k = (int)blockIdx.x / cols;
+  const int x0 = (col % cols_x) * kNTX, y0 = (col / cols_x) * kNTY;
+  const int zb = (int)((long long)k * L.nz / nch), ze = (int)((long long)(k + 1) * L.nz / nch);
+  const int tx = (int)threadIdx.x % kNTX, ty = (int)threadIdx.x / kNTX;
+  const int x = x0 + tx, y = y0 + ty;
+  const bool active = x < L.nx && y < L.ny;
+  n_psi_plane<NC>(D, src, r, zb - 1, x0, y0);
+  n_psi_plane<NC>(D, src, r, zb, x0, y0);
+  for (int p = zb; p < ze; ++p) {
+    n_psi_plane<NC>(D, src, r, p + 1, x0, y0);
+    __syncthreads();
+    if (active && !solid_z(L, p)) n_collide_site<NC>(D, src, dst, r, p, x, y, tx, ty);
   }
 }
 
@@ -189,11 +219,10 @@ __global__ void k_n_rest(const NDev D, const float* __restrict__ rho, float* __r
   }
 }
 
+// Site-parallel kernels (what: 2 canonical, 3 load, 4 rest populations) on `grid` CTAs.
 template <int NC>
-cudaError_t n_launch(int what, const NDev& D, const float* a, float* b, float* c, int grid, cudaStream_t st) {
+cudaError_t n_launch(int what, const NDev& D, const float* a, float* b, int grid, cudaStream_t st) {
   switch (what) {
-    case 0: k_n_psi<NC><<<grid, 256, 0, st>>>(D, a, b); break;
-    case 1: k_n_collide<NC><<<grid, 256, 0, st>>>(D, a, b, c); break;
     case 2: k_n_canonical<NC><<<grid, 256, 0, st>>>(D, a, b); break;
     case 4: k_n_rest<NC><<<grid, 256, 0, st>>>(D, a, b); break;
     default: k_n_load<NC><<<grid, 256, 0, st>>>(D, a, b); break;
@@ -201,13 +230,37 @@ cudaError_t n_launch(int what, const NDev& D, const float* a, float* b, float* c
   return cudaGetLastError();
 }
 
-cudaError_t n_dispatch(int nc, int what, const NDev& D, const float* a, float* b, float* c, int grid,
-                       cudaStream_t st) {
+cudaError_t n_dispatch(int nc, int what, const NDev& D, const float* a, float* b, int grid, cudaStream_t st) {
   switch (nc) {
-    case 2: return n_launch<2>(what, D, a, b, c, grid, st);
-    case 3: return n_launch<3>(what, D, a, b, c, grid, st);
-    default: return n_launch<4>(what, D, a, b, c, grid, st);
+    case 2: return n_launch<2>(what, D, a, b, grid, st);
+    case 3: return n_launch<3>(what, D, a, b, grid, st);
+    default: return n_launch<4>(what, D, a, b, grid, st);
   }
+}
+
+template <int NC>
+cudaError_t n_step_launch(const NDev& D, const float* src, float* dst, int cols_x, int cols, int nch,
+                          cudaStream_t st) {
+  k_n_step<NC><<<cols * nch, kNT, 0, st>>>(D, src, dst, cols_x, cols, nch);
+  return cudaGetLastError();
+}
+
+cudaError_t n_step_dispatch(int nc, const NDev& D, const float* src, float* dst, int cols_x, int cols, int nch,
+                            cudaStream_t st) {
+  switch (nc) {
+    case 2: return n_step_launch<2>(D, src, dst, cols_x, cols, nch, st);
+    case 3: return n_step_launch<3>(D, src, dst, cols_x, cols, nch, st);
+    default: return n_step_launch<4>(D, src, dst, cols_x, cols, nch, st);
+  }
+}
+
+int n_step_occupancy(int nc) {
+  int occ = 0;
+  cudaError_t e = nc == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_n_step<2>, kNT, 0)
+                : nc == 3 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_n_step<3>, kNT, 0)
+                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_n_step<4>, kNT, 0);
+  if (e != cudaSuccess) cudaGetLastError();
+  return e == cudaSuccess ? occ : 0;
 }
 
 }  // namespace
@@ -219,7 +272,8 @@ struct sc_ncomp {
   char* base;
   size_t pop_bytes, off_pop[2], off_psi, total;
   int cur;
-  int grid;
+  int grid;                  // CTAs of the site-parallel kernels
+  int cols_x, cols, nch;     // the step's tile columns and plane chunks (cols * nch CTAs)
   int64_t step;
   float* pop(int k) const { return (float*)(base + off_pop[k]); }
   float* psi() const { return (float*)(base + off_psi); }
@@ -261,6 +315,22 @@ int sc_ncomp_create(const sc_nparams* p, void* stream, sc_ncomp** out) {
   h->total = h->off_psi + align256((size_t)p->ncomp * np * sizeof(float));
   h->stream = (cudaStream_t)stream;
   h->grid = (int)grid_for(l.nsites, 256);
+  // plane chunks: the fewest waves of resident CTAs times the planes (with the two
+  // halo planes) each CTA marches
+  h->cols_x = (p->nx + kNTX - 1) / kNTX;
+  h->cols = h->cols_x * ((p->ny + kNTY - 1) / kNTY);
+  {
+    int dev = 0, sms = 1;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long slots = (long long)std::max(1, sms) * std::max(1, n_step_occupancy(p->ncomp));
+    double best = 1e300;
+    h->nch = 1;
+    for (int nch = 1; nch <= p->nz && (long long)nch * h->cols <= (1LL << 30); ++nch) {
+      const long long waves = ((long long)h->cols * nch + slots - 1) / slots;
+      const double cost = (double)waves * ((p->nz + nch - 1) / nch + 2);
+      if (cost < best * (1.0 - 1e-9)) { best = cost; h->nch = nch; }
+    }
+  }
   cudaError_t e = cudaMalloc((void**)&h->base, h->total);
   if (e != cudaSuccess) {
     delete h;
@@ -293,7 +363,7 @@ int sc_ncomp_write_populations(sc_ncomp* h, const double* f) {
   // staged in the other buffer, which the next step overwrites anyway
   float* stage = h->pop(1 - h->cur);
   CK(cudaMemcpyAsync(stage, tmp.data(), sizeof(float) * m, cudaMemcpyHostToDevice, h->stream));
-  CK(n_dispatch(h->p.ncomp, 3, h->D, stage, h->pop(h->cur), nullptr, h->grid, h->stream));
+  CK(n_dispatch(h->p.ncomp, 3, h->D, stage, h->pop(h->cur), h->grid, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   return SC_OK;
 }
@@ -306,8 +376,8 @@ int sc_ncomp_init_fields(sc_ncomp* h, const float* rho) {
   // populations into the other buffer, then placed where the next pull reads them
   float* stage = h->pop(1 - h->cur);
   CK(cudaMemcpyAsync(h->psi(), rho, sizeof(float) * h->p.ncomp * n, cudaMemcpyHostToDevice, h->stream));
-  CK(n_dispatch(h->p.ncomp, 4, h->D, h->psi(), stage, nullptr, h->grid, h->stream));
-  CK(n_dispatch(h->p.ncomp, 3, h->D, stage, h->pop(h->cur), nullptr, h->grid, h->stream));
+  CK(n_dispatch(h->p.ncomp, 4, h->D, h->psi(), stage, h->grid, h->stream));
+  CK(n_dispatch(h->p.ncomp, 3, h->D, stage, h->pop(h->cur), h->grid, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   h->step = 0;
   return SC_OK;
@@ -320,7 +390,7 @@ int sc_ncomp_read_populations(sc_ncomp* h, double* f) {
   std::vector<float> tmp;
   try { tmp.resize(m); } catch (...) { return fail(SC_ENOMEM, "host allocation failed"); }
   float* stage = h->pop(1 - h->cur);
-  CK(n_dispatch(h->p.ncomp, 2, h->D, h->pop(h->cur), stage, nullptr, h->grid, h->stream));
+  CK(n_dispatch(h->p.ncomp, 2, h->D, h->pop(h->cur), stage, h->grid, h->stream));
   CK(cudaMemcpyAsync(tmp.data(), stage, sizeof(float) * m, cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   for (size_t k = 0; k < m; ++k) f[k] = (double)tmp[k];
@@ -333,8 +403,7 @@ int sc_ncomp_step(sc_ncomp* h, int64_t nsteps) {
   if (nsteps < 0) return fail(SC_EINVAL, "nsteps must be >= 0");
   for (int64_t k = 0; k < nsteps; ++k) {
     const int src = h->cur, dst = 1 - h->cur;
-    CK(n_dispatch(h->p.ncomp, 0, h->D, h->pop(src), h->psi(), nullptr, h->grid, h->stream));
-    CK(n_dispatch(h->p.ncomp, 1, h->D, h->pop(src), h->pop(dst), h->psi(), h->grid, h->stream));
+    CK(n_step_dispatch(h->p.ncomp, h->D, h->pop(src), h->pop(dst), h->cols_x, h->cols, h->nch, h->stream));
     h->cur = dst;
   }
   h->step += nsteps;
