@@ -12,6 +12,8 @@ density effect after n steps is of order 2^-12 sqrt(n) ~ 8e-3 at n = 1000 and
 is damped where the dynamics is diffusive; BF16 has 8 significant bits (8x
 FP16). The tests assert those orders and record the measured values.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -107,3 +109,18 @@ def test_precision_vs_oracle_128(sc, oracle_mod):
     assert out["f16"]["linf"] < 6e-2 and out["f16s"]["linf"] < 6e-2 and out["bf16"]["linf"] < 0.25
     assert out["f16"]["l2"] < 4e-3 and out["f16s"]["l2"] < 4e-3
     assert abs(out["f16"]["radius"] - out["f16"]["radius_oracle"]) < 0.5
+
+
+@pytest.mark.skipif(os.environ.get("SC_PAPER_SCALE") != "1",
+                    reason="5000 oracle steps of a 128^3 lattice (about fifteen minutes): set SC_PAPER_SCALE=1")
+def test_precision_vs_oracle_128_5000(sc, oracle_mod):
+    """The same study over 5000 steps, the run length of the large-droplet precision
+    case. Bounds scale the 1000-step ones: the FP32 rounding linearly in the steps
+    (5x), the FP16 / BF16 store rounding as a random walk (sqrt(5) x)."""
+    out = _study(sc, oracle_mod, 128, 5000)
+    _record("128_5000", out)
+    assert out["f32"]["linf"] < 5e-4
+    assert abs(out["f32"]["radius"] - out["f32"]["radius_oracle"]) < 5e-3
+    assert out["f16"]["linf"] < 0.14 and out["f16s"]["linf"] < 0.14 and out["bf16"]["linf"] < 0.56
+    assert out["f16"]["l2"] < 9e-3 and out["f16s"]["l2"] < 9e-3
+    assert abs(out["f16"]["radius"] - out["f16"]["radius_oracle"]) < 1.12
