@@ -455,16 +455,20 @@ def oracle_sample(args, params, init):
 
 def precision_record():
     """Error against the FP64 oracle of each storage type on the 128^3 crop-equivalent
-    droplet after 1000 steps, from the committed summary of the precision study
-    (tests/test_gpu_precision.py), or None."""
-    for kv in profile_fields():
-        if kv.get("study") == "precision_droplet_128":
-            rec = {"source": f"profiles/{kv['file']}", "case": kv.get("case")}
-            for st in ("f32", "f16", "bf16", "f16s"):
-                if f"{st}_linf" in kv:
-                    rec[st] = {"density_linf": float(kv[f"{st}_linf"]), "density_l2": float(kv[f"{st}_l2"]),
-                               "radius_error": float(kv[f"{st}_radius_error"])}
-            return rec
+    droplet, from the committed summary of the precision study
+    (tests/test_gpu_precision.py): the 5000-step study when it is recorded, else the
+    1000-step one; None when neither is."""
+    fields = {kv.get("study"): kv for kv in profile_fields()}
+    for study in ("precision_droplet_128_5000", "precision_droplet_128"):
+        kv = fields.get(study)
+        if kv is None:
+            continue
+        rec = {"source": f"profiles/{kv['file']}", "case": kv.get("case")}
+        for st in ("f32", "f16", "bf16", "f16s"):
+            if f"{st}_linf" in kv:
+                rec[st] = {"density_linf": float(kv[f"{st}_linf"]), "density_l2": float(kv[f"{st}_l2"]),
+                           "radius_error": float(kv[f"{st}_radius_error"])}
+        return rec
     return None
 
 

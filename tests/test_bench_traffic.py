@@ -100,3 +100,14 @@ def test_slab_layout_config(bench):
     c = bench.arm_config(a, 4)
     assert c == bench.arm_config(b, 4) and c["layout"] == "slab"
     assert "split along z over 4 ranks" in c["parallelism"] and str(2 * 19 * 2 * 128 * 128 * 4) in c["parallelism"]
+
+
+def test_precision_record_prefers_the_longer_study(bench, tmp_path, monkeypatch):
+    for study, case in (("precision_droplet_128", "1000 steps"), ("precision_droplet_128_5000", "5000 steps")):
+        (tmp_path / f"{study}.md").write_text(f"- study: `{study}`\n- case: `{case}`\n- f32_linf: `1e-6`\n"
+                                              f"- f32_l2: `1e-7`\n- f32_radius_error: `0.0`\n")
+    monkeypatch.setattr(bench, "PROFILE_DIR", str(tmp_path))
+    assert bench.precision_record()["case"] == "5000 steps"
+    (tmp_path / "precision_droplet_128_5000.md").unlink()
+    rec = bench.precision_record()
+    assert rec["case"] == "1000 steps" and rec["f32"]["density_linf"] == 1e-6
