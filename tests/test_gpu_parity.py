@@ -327,3 +327,20 @@ def test_full_size_sampled_windows(sc, oracle_mod, n, radius, seed, tuned):
         orr, ob = o.fields()
         assert abs(r1[Z, Y, X] - orr[3, 3, 3]) < 1e-6 * max(1.0, orr[3, 3, 3]), (X, Y, Z)
         assert abs(b1[Z, Y, X] - ob[3, 3, 3]) < 1e-6 * max(1.0, ob[3, 3, 3]), (X, Y, Z)
+
+
+@pytest.mark.parametrize("layout", ["two", "aa"])
+def test_close_releases_device_memory(sc, layout):
+    """Lattice.close destroys the handle after its stream has finished and gives its
+    device memory back to torch's allocator."""
+    import torch
+    from paper_1701_03637_gb300.workloads import droplet
+    params, init = droplet(64, 12.0, 1)
+    torch.cuda.synchronize()
+    before = torch.cuda.memory_allocated()
+    lat = sc.Lattice(dict(params, layout=layout))
+    lat.init(init)
+    lat.step(3)
+    assert torch.cuda.memory_allocated() - before >= sc.required_bytes(dict(params, layout=layout))
+    lat.close()
+    assert torch.cuda.memory_allocated() == before
