@@ -90,3 +90,13 @@ def test_in_place_layout_holds_one_lattice(native):
     device = 284208 * 2 ** 20
     assert sc.required_bytes(dict(nx=1024, ny=1024, nz=1024, layout="aa")) < 0.7 * device
     assert sc.required_bytes(dict(nx=1024, ny=1024, nz=1024)) > device
+
+
+def test_null_handles_rejected_without_a_device(native):
+    """Entry points that take a handle reject NULL with SC_EINVAL before any device call."""
+    lib = native.load()
+    assert lib.sc_lbm_persist_bands(None, -1, None) == -1
+    assert lib.sc_lbm_persist_bands(None, 2, None) == -1
+    assert lib.sc_lbm_set_wait(None, 1000, -1) == -1
+    assert lib.sc_ncomp_init_fields(None, None) == -1
+    assert lib.sc_ncomp_step(None, 1) == -1
