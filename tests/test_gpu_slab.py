@@ -2,7 +2,7 @@
 device, exchanging their ghost planes through the library's pack/unpack and device
 copies before every step, hold in their own planes exactly what one lattice stepped
 by sc_lbm_step holds (walls, planar sinks across the periodic seam, the spherical
-sink, self couplings, FP32 and FP16 storage), from the seeded initial state of the
+sink, self couplings, FP32, FP16, BF16 and scaled FP16 storage), from the seeded initial state of the
 whole lattice; their diagnostics add up to the whole lattice's."""
 import numpy as np
 import pytest
@@ -39,7 +39,7 @@ def _cases():
 CASES = _cases()
 
 
-@pytest.mark.parametrize("storage", ["f32", "f16"])
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16", "f16s"])
 @pytest.mark.parametrize("parts", [2, 3, 5])
 @pytest.mark.parametrize("case", list(CASES))
 def test_slabs_equal_one_lattice(sc, case, parts, storage):
