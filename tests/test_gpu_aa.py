@@ -104,7 +104,7 @@ BANDS = {"seam_sink_unequal_tau": [2, 4, 16], "periodic_two_segments": [2, 5, 65
          "self_couplings_sphere_sink": [2, 5, 10], "film_wall_sink": [2]}
 
 
-@pytest.mark.parametrize("storage", ["f32", "f16"])
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16", "f16s"])
 @pytest.mark.parametrize("case,bands", [(c, b) for c, bs in BANDS.items() for b in bs])
 def test_bands_same_bits_as_two_lattices(sc, case, bands, storage):
     """The persistent step marching the lattice in x-bands, one after another (halo
