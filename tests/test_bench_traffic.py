@@ -85,7 +85,8 @@ def test_l2_note_is_true_for_small_lattices(bench):
 
 
 @pytest.mark.parametrize("argv", [[], ["--workload", "droplet_128"], ["--workload", "ensemble_64"],
-                                  ["--workload", "serve"], ["--workload", "film_4x4x128", "--storage", "f16"]])
+                                  ["--workload", "serve"], ["--workload", "film_4x4x128", "--storage", "f16"],
+                                  ["--workload", "ncomp3_128"], ["--workload", "droplet_1024"]])
 def test_both_arms_print_the_same_config(bench, argv):
     """The oracle arm's config is computed by the same function from the same
     arguments: nothing in it depends on which arm runs."""
@@ -111,3 +112,10 @@ def test_precision_record_prefers_the_longer_study(bench, tmp_path, monkeypatch)
     (tmp_path / "precision_droplet_128_5000.md").unlink()
     rec = bench.precision_record()
     assert rec["case"] == "1000 steps" and rec["f32"]["density_linf"] == 1e-6
+
+
+def test_three_component_config(bench):
+    a = _args(bench, ["--workload", "ncomp3_128"])
+    c = bench.arm_config(a, 2)
+    assert c["components"] == 3 and c["sites"] == 128 ** 3 and c["layout"] == "two"
+    assert c["l2"].startswith("inputs larger than L2") and "replicas x2" in c["parallelism"]
